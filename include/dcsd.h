@@ -1,0 +1,181 @@
+/*
+ * dcsd.h -- C ABI of the GB300 two-determinant CCSD / DCSD residual engine.
+ *
+ * The method is 2D-CCSD and its distinguishable-cluster variant 2D-DCSD of
+ * Schraivogel & Kats, "Two Determinant Distinguishable Cluster" (arXiv
+ * 2401.11935), Section II, Eqs. 2-4: the singles/doubles amplitude residuals
+ * of an open-shell singlet or M_s = 0 triplet built on the two determinants
+ * Phi_A (core^2, t alpha, u beta) and Phi_B (core^2, u alpha, t beta) of
+ * Fig. 1, with the coupling W and the 2x2 effective Hamiltonian whose
+ * eigenvalues are the singlet (dE_A + W) and triplet (dE_A - W) energies.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Spatial orbitals (n = n_c + 2 + n_v): core 0..n_c-1, t = n_c, u = n_c+1,
+ * external virtuals n_c+2..n-1.  Two-electron integrals are density fitted:
+ * (pq|rs) = sum_L B[L][p][q] B[L][r][s], B symmetric in (p,q).
+ *
+ * Amplitudes and residuals are normal-ordered to Phi_A (ref = 0) or Phi_B
+ * (ref = 1).  With o = n_c + 1 and v = n_v + 1 per spin, the per-spin index
+ * lists are
+ *     ref 0: alpha occ (core..., t)  beta occ (core..., u)
+ *            alpha vir (u, V...)     beta vir (t, V...)
+ *     ref 1: alpha occ (core..., u)  beta occ (core..., t)
+ *            alpha vir (t, V...)     beta vir (u, V...)
+ * and the arrays are row-major doubles
+ *     T1a, T1b  [o][v]
+ *     T2aa, T2bb [o][o][v][v]   antisymmetric in (i,j) and in (a,b)
+ *     T2ab      [o][o][v][v]    (alpha occ i, beta occ j, alpha vir a, beta vir b).
+ * The excitation Phi_ref -> the other determinant is T2ab[o-1][o-1][0][0]
+ * in both frames; its amplitude must be zero (Section II, text after Eq. 4).
+ * Fock matrices passed to dcsd_init are those of Phi_A; for ref = 1 the
+ * library uses the alpha matrix as beta and vice versa (spin flip).
+ *
+ * Ownership and errors: every function returns a dcsd_status; no exception
+ * or abort crosses the ABI.  A context owns all device memory it allocates
+ * (freed by dcsd_destroy).  Pointers passed to a call are borrowed for the
+ * duration of that call only.  Device pointers must stay valid until the
+ * work enqueued on the context's stream has finished.  dcsd_last_error
+ * returns a message owned by the context, valid until the next call.
+ */
+#ifndef DCSD_H
+#define DCSD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DCSD_OK = 0,
+    DCSD_ERR_INVALID_ARG = 1,  /* bad pointer, size, enum value or layout  */
+    DCSD_ERR_OOM = 2,          /* device allocation failed                 */
+    DCSD_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed        */
+    DCSD_ERR_NOT_CONVERGED = 4,/* dcsd_solve hit maxiter                   */
+    DCSD_ERR_TIMEOUT = 5,      /* a bounded device wait gave up            */
+    DCSD_ERR_NUMERIC = 6,      /* NaN/Inf in a residual or energy          */
+    DCSD_ERR_NO_DEVICE = 7     /* no CUDA device of compute capability 10.3 */
+} dcsd_status;
+
+typedef enum { DCSD_CCSD = 0, DCSD_DCSD = 1 } dcsd_method;
+typedef enum { DCSD_MEM_HOST = 0, DCSD_MEM_DEVICE = 1 } dcsd_mem_kind;
+
+/* Arithmetic of the dense contractions (ladder, ring, DF builds).  The
+ * orbital-energy denominators, DIIS, energies, residual norm and the 2x2
+ * effective Hamiltonian are always FP64. */
+typedef enum {
+    DCSD_PREC_FP64 = 0,   /* FP64 on CUDA cores                              */
+    DCSD_PREC_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 acc */
+    DCSD_PREC_BF16X3 = 2, /* split operands hi+lo, 3 BF16 products (FP32x2)  */
+    DCSD_PREC_MIXED = 3   /* dcsd_solve only: BF16, then BF16X3 below switch */
+} dcsd_precision;
+
+typedef struct dcsd_ctx dcsd_ctx;
+
+typedef struct {
+    int n_c;   /* doubly occupied (correlated) spatial orbitals, >= 0 */
+    int n_v;   /* external virtual spatial orbitals, >= 1            */
+    int naux;  /* density-fitting functions, >= 1                    */
+} dcsd_dims;
+
+typedef struct {
+    int method;         /* dcsd_method                                      */
+    int ref;            /* 0 = Phi_A, 1 = Phi_B                             */
+    int precision;      /* dcsd_precision                                   */
+    int maxiter;        /* iteration cap (e.g. 100)                         */
+    int diis_n;         /* DIIS history length, 0..16 (0 = Jacobi only)     */
+    double tol;         /* convergence: max |R| <= tol                      */
+    double switch_tol;  /* MIXED: switch BF16 -> BF16X3 when max|R| < this  */
+    int use_guess;      /* 1: start from the T passed in, 0: from T = 0      */
+} dcsd_solve_opts;
+
+typedef struct {
+    double dEA;       /* Delta E_A = <A|H_N exp(T_A)|A>  (Eq. 2)            */
+    double W;         /* <B|H_N exp(T_A)|A>, coupling of the two references */
+    double E_S;       /* singlet correlation energy dE_A + W                */
+    double E_T;       /* triplet correlation energy dE_A - W                */
+    double max_r;     /* max |R| of the last residual                       */
+    int iters;        /* residual evaluations performed                     */
+    int converged;    /* 1 if max_r <= tol                                   */
+    double seconds;   /* wall time of the solve                             */
+    int switched_at;  /* MIXED: iteration of the precision switch, or -1    */
+} dcsd_result;
+
+/* dcsd_init -- create a context (Section II inputs of the method).
+ *   out    : receives the context (NULL on error).
+ *   d      : sizes.
+ *   eps    : [n] orbital energies (informational; denominators are taken
+ *            from the Fock diagonals).  May be NULL.
+ *   fock_a, fock_b : [n][n] row-major Fock matrices of alpha and beta spin
+ *            w.r.t. Phi_A (frozen-core contributions included).
+ *   B      : [naux][n][n] DF factors, symmetric in the last two indices.
+ *   mem_kind : whether eps/fock/B are host or device pointers; the library
+ *            copies them.
+ *   stream : cudaStream_t every call of this context enqueues on (NULL =
+ *            legacy default stream).
+ * Allocates all device memory the context needs for FP64 and BF16 paths.
+ * Errors: INVALID_ARG (sizes < bounds, NULL pointers), OOM, CUDA, NO_DEVICE. */
+dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const double* eps,
+                      const double* fock_a, const double* fock_b,
+                      const double* B, int mem_kind, void* stream);
+
+/* dcsd_residual -- one evaluation of the 2D residual (Eqs. 3-4).
+ *   R = R^X(T) + M W with R^X the CCSD (method 0) or DCSD (method 1)
+ *   single-reference residual; W = R^X at the A->B double; that element of
+ *   R2ab is returned as zero.  dEA receives Delta E_A (Eq. 2).
+ *   T* inputs and R* outputs use the layouts above; mem_kind says whether
+ *   they are host (copied in and out inside the call, which then
+ *   synchronises the stream) or device pointers (asynchronous on the
+ *   context stream; W and dEA are still host doubles and the call
+ *   synchronises before returning them).  Outputs may not alias inputs.
+ *   precision: DCSD_PREC_FP64, _BF16 or _BF16X3.
+ * Errors: INVALID_ARG, CUDA, NUMERIC (NaN/Inf in R). */
+dcsd_status dcsd_residual(dcsd_ctx* ctx, int ref, int method, int precision,
+                          int mem_kind,
+                          const double* T1a, const double* T1b,
+                          const double* T2aa, const double* T2bb,
+                          const double* T2ab,
+                          double* R1a, double* R1b, double* R2aa,
+                          double* R2bb, double* R2ab,
+                          double* W, double* dEA);
+
+/* dcsd_energy -- Delta E_A (Eq. 2) and W for the amplitudes T (same layout
+ * and mem_kind rules as dcsd_residual; FP64).  W needs the doubles residual
+ * element of the A->B excitation, so this runs one FP64 residual. */
+dcsd_status dcsd_energy(dcsd_ctx* ctx, int ref, int method, int mem_kind,
+                        const double* T1a, const double* T1b,
+                        const double* T2aa, const double* T2bb,
+                        const double* T2ab, double* dEA, double* W);
+
+/* dcsd_solve -- converge the 2D amplitude equations on the GPU (Jacobi
+ * steps with Fock-diagonal denominators + Pulay DIIS, all FP64 vector
+ * algebra on the device).  T* are in/out (initial guess if
+ * opts->use_guess, converged amplitudes on return), mem_kind as above.
+ * Returns NOT_CONVERGED (with T and *res filled) if maxiter is reached. */
+dcsd_status dcsd_solve(dcsd_ctx* ctx, const dcsd_solve_opts* opts, int mem_kind,
+                       double* T1a, double* T1b, double* T2aa, double* T2bb,
+                       double* T2ab, dcsd_result* res);
+
+/* dcsd_heff -- the 2x2 effective Hamiltonian of the two references (Eq. 2
+ * and the text after Eq. 4): H = [[dEA, W], [W, dEA]] (row-major H[4]),
+ * its eigenvalues in ascending order evals[2], and *singlet_index, the
+ * position of the singlet dEA + W in evals.  Pure host arithmetic. */
+dcsd_status dcsd_heff(double dEA, double W, double* H, double* evals,
+                      int* singlet_index);
+
+/* dcsd_destroy -- free the context and all its device memory (NULL ok). */
+dcsd_status dcsd_destroy(dcsd_ctx* ctx);
+
+/* dcsd_last_error -- human-readable message of the last failed call of
+ * ctx (or of the last failed dcsd_init when ctx is NULL). */
+const char* dcsd_last_error(const dcsd_ctx* ctx);
+
+/* dcsd_kernel_launches -- number of kernels this context has launched since
+ * creation (diagnostics / benchmark accounting). */
+long long dcsd_kernel_launches(const dcsd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCSD_H */

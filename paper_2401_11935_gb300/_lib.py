@@ -1,0 +1,133 @@
+"""ctypes binding of include/dcsd.h (argument marshalling only).
+
+The functions below carry the C names and forward their arguments to
+libdcsd.so; every step of the method runs in the library's CUDA kernels.
+Loading fails loudly if the library has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdcsd.so")
+
+DCSD_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT",
+          6: "NUMERIC", 7: "NO_DEVICE"}
+CCSD, DCSD = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED = 0, 1, 2, 3
+
+EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
+           "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches"]
+
+
+class dcsd_dims(C.Structure):
+    _fields_ = [("n_c", C.c_int), ("n_v", C.c_int), ("naux", C.c_int)]
+
+
+class dcsd_solve_opts(C.Structure):
+    _fields_ = [("method", C.c_int), ("ref", C.c_int), ("precision", C.c_int),
+                ("maxiter", C.c_int), ("diis_n", C.c_int), ("tol", C.c_double),
+                ("switch_tol", C.c_double), ("use_guess", C.c_int)]
+
+
+class dcsd_result(C.Structure):
+    _fields_ = [("dEA", C.c_double), ("W", C.c_double), ("E_S", C.c_double),
+                ("E_T", C.c_double), ("max_r", C.c_double), ("iters", C.c_int),
+                ("converged", C.c_int), ("seconds", C.c_double), ("switched_at", C.c_int)]
+
+
+class DcsdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dcsd status {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2401_11935_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    lib.dcsd_init.argtypes = [C.POINTER(P), C.POINTER(dcsd_dims), P, P, P, P, C.c_int, P]
+    lib.dcsd_residual.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10 + [D, D]
+    lib.dcsd_energy.argtypes = [P, C.c_int, C.c_int, C.c_int] + [P] * 5 + [D, D]
+    lib.dcsd_solve.argtypes = [P, C.POINTER(dcsd_solve_opts), C.c_int] + [P] * 5 + [C.POINTER(dcsd_result)]
+    lib.dcsd_heff.argtypes = [C.c_double, C.c_double, D, D, C.POINTER(C.c_int)]
+    lib.dcsd_destroy.argtypes = [P]
+    lib.dcsd_last_error.argtypes = [P]
+    lib.dcsd_last_error.restype = C.c_char_p
+    lib.dcsd_kernel_launches.argtypes = [P]
+    lib.dcsd_kernel_launches.restype = C.c_longlong
+    for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != DCSD_OK:
+        msg = load().dcsd_last_error(ctx).decode(errors="replace")
+        raise DcsdError(status, msg)
+
+
+def dcsd_init(n_c, n_v, naux, eps, fock_a, fock_b, B, mem_kind, stream):
+    """Create a context; pointers are ints (host or device addresses)."""
+    lib = load()
+    ctx = C.c_void_p()
+    d = dcsd_dims(n_c, n_v, naux)
+    st = lib.dcsd_init(C.byref(ctx), C.byref(d), eps, fock_a, fock_b, B, mem_kind, stream)
+    _check(st, None)
+    return ctx
+
+
+def dcsd_residual(ctx, ref, method, precision, mem_kind, T, R):
+    lib = load()
+    W, dE = C.c_double(), C.c_double()
+    st = lib.dcsd_residual(ctx, ref, method, precision, mem_kind, *T, *R, C.byref(W), C.byref(dE))
+    _check(st, ctx)
+    return W.value, dE.value
+
+
+def dcsd_energy(ctx, ref, method, mem_kind, T):
+    lib = load()
+    W, dE = C.c_double(), C.c_double()
+    st = lib.dcsd_energy(ctx, ref, method, mem_kind, *T, C.byref(dE), C.byref(W))
+    _check(st, ctx)
+    return dE.value, W.value
+
+
+def dcsd_solve(ctx, opts, mem_kind, T, allow_not_converged=True):
+    lib = load()
+    res = dcsd_result()
+    st = lib.dcsd_solve(ctx, C.byref(opts), mem_kind, *T, C.byref(res))
+    if not (allow_not_converged and st == 4):
+        _check(st, ctx)
+    return res
+
+
+def dcsd_heff(dEA, W):
+    lib = load()
+    H = (C.c_double * 4)()
+    ev = (C.c_double * 2)()
+    si = C.c_int()
+    _check(lib.dcsd_heff(dEA, W, H, ev, C.byref(si)))
+    return [H[0], H[1], H[2], H[3]], [ev[0], ev[1]], si.value
+
+
+def dcsd_destroy(ctx):
+    _check(load().dcsd_destroy(ctx))
+
+
+def dcsd_kernel_launches(ctx):
+    return load().dcsd_kernel_launches(ctx)

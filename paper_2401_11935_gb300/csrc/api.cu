@@ -1,0 +1,576 @@
+// C ABI entry points (include/dcsd.h): context management, residual/energy
+// calls, the on-device Jacobi + DIIS solver and the 2x2 effective
+// Hamiltonian of the two references (arXiv 2401.11935, Section II).
+#include "common.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+using namespace dcsd;
+
+static std::string g_init_error;
+
+namespace dcsd {
+
+// Jacobi step on the concatenated union vector [t1 (2*O*V) | t2 (3*O*O*V*V)]:
+// step = -R / D with D the Fock-diagonal orbital-energy differences of the
+// frame (zero where R is zero: padding, masked and symmetry-forbidden
+// elements); tnew = t + step.
+__global__ void k_jacobi(int n, int nc, int O, int V, const double* fa, const double* fb,
+                         const double* t, const double* R, double* tnew, double* step) {
+    const long n1 = 2l * O * V, nb = (long)O * O * V * V, total = n1 + 3 * nb;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        double r = R[e], st = 0.0;
+        if (r != 0.0) {
+            double D;
+            if (e < n1) {
+                int s = (int)(e / ((long)O * V));
+                int i = (int)((e / V) % O), a = (int)(e % V);
+                const double* f = s == 0 ? fa : fb;
+                D = f[(long)(nc + a) * n + nc + a] - f[(long)i * n + i];
+            } else {
+                long r2 = e - n1;
+                int blk = (int)(r2 / nb);
+                r2 -= blk * nb;
+                int b = (int)(r2 % V);
+                r2 /= V;
+                int a = (int)(r2 % V);
+                r2 /= V;
+                int j = (int)(r2 % O);
+                int i = (int)(r2 / O);
+                const double* f1 = blk == 1 ? fb : fa;
+                const double* f2 = blk == 0 ? fa : fb;
+                D = f1[(long)(nc + a) * n + nc + a] + f2[(long)(nc + b) * n + nc + b] -
+                    f1[(long)i * n + i] - f2[(long)j * n + j];
+            }
+            st = -r / D;
+        }
+        step[e] = st;
+        tnew[e] = t[e] + st;
+    }
+}
+
+__global__ void k_maxabs_partial(const double* p, long n, double* part) {
+    __shared__ double sh[256];
+    double m = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(p[e]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_maxabs_final(const double* part, int n, double* out) {
+    __shared__ double sh[256];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, part[i]);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+struct LinComb {
+    const double* v[16];
+    double coef[16];
+    int m;
+};
+
+__global__ void k_lincomb(LinComb lc, long n, double* out) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < lc.m; ++k) s += lc.coef[k] * lc.v[k][e];
+        out[e] = s;
+    }
+}
+
+static unsigned grid_n(Ctx* c, long n) {
+    long g = (n + 255) / 256, cap = (long)std::max(c->num_sms, 1) * 16;
+    return (unsigned)std::max<long>(1, std::min(g, cap));
+}
+
+static dcsd_status maxabs(Ctx* c, const double* p, long n, double* out) {
+    k_maxabs_partial<<<512, 256, 0, c->stream>>>(p, n, c->red);
+    DCSD_TRY(launch_check(c, "maxabs_partial"));
+    k_maxabs_final<<<1, 256, 0, c->stream>>>(c->red, 512, out);
+    return launch_check(c, "maxabs_final");
+}
+
+}  // namespace dcsd
+
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AbiBufs {
+    double* p[5] = {};
+};
+
+long abi_len(const Ctx* c, int k) {
+    return k < 2 ? (long)c->o * c->v : (long)c->o * c->o * c->v * c->v;
+}
+
+dcsd_status alloc(Ctx* c, double** p, size_t n) {
+    if (cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "cudaMalloc of " + std::to_string(n * sizeof(double)) + " bytes failed";
+        return DCSD_ERR_OOM;
+    }
+    return DCSD_OK;
+}
+
+void free_ctx(Ctx* c) {
+    double** ptrs[] = {&c->B, &c->fock[0], &c->fock[1], &c->Kref[0][0], &c->Kref[0][1],
+                       &c->Kref[1][0], &c->Kref[1][1], &c->t1, &c->R1, &c->Bd, &c->Pbt, &c->fd,
+                       &c->fsc, &c->Z, &c->J, &c->H, &c->G, &c->Wo, &c->Foc, &c->Fvi, &c->big0,
+                       &c->big1, &c->big2, &c->big3, &c->red, &c->scal, &c->c1, &c->diis_t,
+                       &c->diis_e, &c->abi[0], &c->abi[1], &c->abi[2], &c->abi[3], &c->abi[4],
+                       &c->abi[5], &c->abi[6], &c->abi[7], &c->abi[8], &c->abi[9]};
+    for (auto pp : ptrs) {
+        if (*pp) cudaFree(*pp);
+        *pp = nullptr;
+    }
+    c->t2 = nullptr;
+    c->R2 = nullptr;
+    if (c->hostbuf) cudaFreeHost(c->hostbuf);
+    c->hostbuf = nullptr;
+    mtables_free(c);
+    tc_free(c);
+}
+
+// device ABI staging (host mem_kind)
+dcsd_status ensure_abi(Ctx* c) {
+    if (c->abi[0]) return DCSD_OK;
+    for (int k = 0; k < 10; ++k) DCSD_TRY(alloc(c, &c->abi[k], abi_len(c, k % 5)));
+    return DCSD_OK;
+}
+
+dcsd_status sync_scalars(Ctx* c, int count) {
+    DCSD_CUDA(c, cudaMemcpyAsync(c->hostbuf, c->scal, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return DCSD_OK;
+}
+
+bool valid_prec(int p) { return p == DCSD_PREC_FP64 || p == DCSD_PREC_BF16 || p == DCSD_PREC_BF16X3; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const double* eps,
+                                 const double* fock_a, const double* fock_b, const double* B,
+                                 int mem_kind, void* stream) {
+    (void)eps;
+    if (!out) {
+        g_init_error = "out is NULL";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!d || !fock_a || !fock_b || !B) {
+        g_init_error = "NULL argument";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    if (d->n_c < 0 || d->n_v < 1 || d->naux < 1 || (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
+        g_init_error = "invalid dimensions or mem_kind";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_init_error = "no CUDA device";
+        return DCSD_ERR_NO_DEVICE;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    if (prop.major != 10 || prop.minor != 3) {
+        g_init_error = "device is sm_" + std::to_string(prop.major) + std::to_string(prop.minor) +
+                       "; this library is built for sm_103a (GB300)";
+        return DCSD_ERR_NO_DEVICE;
+    }
+    dcsd_ctx* h = new dcsd_ctx();
+    Ctx* c = &h->c;
+    c->device = dev;
+    c->num_sms = prop.multiProcessorCount;
+    c->stream = (cudaStream_t)stream;
+    c->nc = d->n_c;
+    c->nv = d->n_v;
+    c->X = d->naux;
+    c->n = c->nc + 2 + c->nv;
+    c->O = c->nc + 2;
+    c->V = c->nv + 2;
+    c->o = c->nc + 1;
+    c->v = c->nv + 1;
+    const size_t n = c->n, O = c->O, V = c->V, X = c->X;
+    const size_t OV = O * V, n1 = 2 * OV, n2 = 3 * OV * OV;
+    c->big_elems = std::max({OV * OV, V * V * V, X * OV, O * O * O * V, (size_t)16});
+    auto fail = [&](dcsd_status s) {
+        g_init_error = c->err;
+        free_ctx(c);
+        delete h;
+        return s;
+    };
+    dcsd_status st = DCSD_OK;
+#define A_(p, cnt) if ((st = alloc(c, &(p), (cnt))) != DCSD_OK) return fail(st)
+    A_(c->B, X * n * n);
+    A_(c->fock[0], n * n);
+    A_(c->fock[1], n * n);
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) A_(c->Kref[r][s], n * n);
+    A_(c->t1, n1 + n2);
+    c->t2 = c->t1 + n1;
+    A_(c->R1, n1 + n2);
+    c->R2 = c->R1 + n1;
+    A_(c->c1, n1);
+    A_(c->Bd, 2 * X * n * n);
+    A_(c->Pbt, X * n * O);
+    A_(c->fd, 2 * n * n);
+    A_(c->fsc, 7 * n * n + X + 16);
+    A_(c->Z, 2 * X * OV);
+    A_(c->J, OV * OV);
+    A_(c->H, 3 * O * O * O * O);
+    A_(c->G, 4 * O * O * O * V);
+    A_(c->Wo, O * O * O * O);
+    A_(c->Foc, 2 * O * O);
+    A_(c->Fvi, 2 * V * V);
+    A_(c->big0, c->big_elems);
+    A_(c->big1, c->big_elems);
+    A_(c->big2, c->big_elems);
+    A_(c->big3, c->big_elems);
+    A_(c->red, 1024);
+    A_(c->scal, 64);
+#undef A_
+    if (cudaMallocHost((void**)&c->hostbuf, 64 * sizeof(double)) != cudaSuccess) {
+        c->err = "cudaMallocHost failed";
+        return fail(DCSD_ERR_OOM);
+    }
+    cudaMemcpyKind kind = mem_kind == DCSD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(c->B, B, X * n * n * sizeof(double), kind, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->fock[0], fock_a, n * n * sizeof(double), kind, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->fock[1], fock_b, n * n * sizeof(double), kind, c->stream) != cudaSuccess) {
+        c->err = std::string("input copy failed: ") + cudaGetErrorString(cudaGetLastError());
+        return fail(DCSD_ERR_CUDA);
+    }
+    if ((st = init_constants(c)) != DCSD_OK) return fail(st);
+    if ((st = mtables_build(c)) != DCSD_OK) return fail(st);
+    if ((st = tc_init(c)) != DCSD_OK) return fail(st);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        c->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
+        return fail(DCSD_ERR_CUDA);
+    }
+    *out = h;
+    return DCSD_OK;
+}
+
+extern "C" dcsd_status dcsd_destroy(dcsd_ctx* h) {
+    if (!h) return DCSD_OK;
+    Ctx* c = &h->c;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    delete h;
+    return DCSD_OK;
+}
+
+extern "C" const char* dcsd_last_error(const dcsd_ctx* h) {
+    if (!h) return g_init_error.c_str();
+    return h->c.err.c_str();
+}
+
+extern "C" long long dcsd_kernel_launches(const dcsd_ctx* h) { return h ? h->c.launches : 0; }
+
+static dcsd_status residual_common(Ctx* c, int ref, int method, int prec, int mem_kind,
+                                   const double* const* T, double* const* R, double* W, double* dEA) {
+    if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) || !valid_prec(prec) ||
+        (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
+        c->err = "invalid ref/method/precision/mem_kind";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 5; ++k)
+        if (!T[k]) {
+            c->err = "NULL amplitude pointer";
+            return DCSD_ERR_INVALID_ARG;
+        }
+    const double* Td[5];
+    double* Rd[5] = {};
+    if (mem_kind == DCSD_MEM_HOST) {
+        DCSD_TRY(ensure_abi(c));
+        for (int k = 0; k < 5; ++k) {
+            DCSD_CUDA(c, cudaMemcpyAsync(c->abi[k], T[k], abi_len(c, k) * sizeof(double),
+                                         cudaMemcpyHostToDevice, c->stream));
+            Td[k] = c->abi[k];
+            Rd[k] = c->abi[5 + k];
+        }
+    } else {
+        for (int k = 0; k < 5; ++k) {
+            Td[k] = T[k];
+            Rd[k] = R ? R[k] : nullptr;
+        }
+    }
+    DCSD_TRY(unpack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]));
+    DCSD_TRY(residual_union(c, ref, method, prec));
+    if (R) {
+        for (int k = 0; k < 5; ++k)
+            if (!R[k]) {
+                c->err = "NULL residual pointer";
+                return DCSD_ERR_INVALID_ARG;
+            }
+        DCSD_TRY(pack_R(c, ref, Rd[0], Rd[1], Rd[2], Rd[3], Rd[4]));
+    }
+    DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
+    DCSD_TRY(check_finite(c, c->R1, 2ul * c->O * c->V + 3ul * c->O * c->O * c->V * c->V, c->scal + 20));
+    if (mem_kind == DCSD_MEM_HOST && R) {
+        for (int k = 0; k < 5; ++k)
+            DCSD_CUDA(c, cudaMemcpyAsync(R[k], Rd[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+    }
+    DCSD_TRY(sync_scalars(c, 21));
+    if (W) *W = c->hostbuf[0];
+    if (dEA) *dEA = c->hostbuf[1];
+    if (c->hostbuf[20] != 0.0 || !std::isfinite(c->hostbuf[0]) || !std::isfinite(c->hostbuf[1])) {
+        c->err = "non-finite residual";
+        return DCSD_ERR_NUMERIC;
+    }
+    return DCSD_OK;
+}
+
+extern "C" dcsd_status dcsd_residual(dcsd_ctx* h, int ref, int method, int precision, int mem_kind,
+                                     const double* T1a, const double* T1b, const double* T2aa,
+                                     const double* T2bb, const double* T2ab, double* R1a, double* R1b,
+                                     double* R2aa, double* R2bb, double* R2ab, double* W, double* dEA) {
+    if (!h) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
+    double* R[5] = {R1a, R1b, R2aa, R2bb, R2ab};
+    for (int k = 0; k < 5; ++k)
+        if (!R[k]) {
+            c->err = "NULL residual pointer";
+            return DCSD_ERR_INVALID_ARG;
+        }
+    return residual_common(c, ref, method, precision, mem_kind, T, R, W, dEA);
+}
+
+extern "C" dcsd_status dcsd_energy(dcsd_ctx* h, int ref, int method, int mem_kind, const double* T1a,
+                                   const double* T1b, const double* T2aa, const double* T2bb,
+                                   const double* T2ab, double* dEA, double* W) {
+    if (!h) return DCSD_ERR_INVALID_ARG;
+    const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
+    return residual_common(&h->c, ref, method, DCSD_PREC_FP64, mem_kind, T, nullptr, W, dEA);
+}
+
+extern "C" dcsd_status dcsd_heff(double dEA, double W, double* H, double* evals, int* singlet_index) {
+    if (!H || !evals || !singlet_index) return DCSD_ERR_INVALID_ARG;
+    H[0] = dEA; H[1] = W; H[2] = W; H[3] = dEA;
+    double lo = dEA - std::fabs(W), hi = dEA + std::fabs(W);
+    evals[0] = lo;
+    evals[1] = hi;
+    *singlet_index = W >= 0.0 ? 1 : 0;  // the singlet is dEA + W
+    return DCSD_OK;
+}
+
+// small dense solve (partial pivoting) of the DIIS system
+static bool solve_small(int m, std::vector<double> A, std::vector<double> b, std::vector<double>& x) {
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < m; ++i)
+            if (std::fabs(A[i * m + k]) > std::fabs(A[piv * m + k])) piv = i;
+        if (std::fabs(A[piv * m + k]) < 1e-300) return false;
+        if (piv != k) {
+            for (int j = 0; j < m; ++j) std::swap(A[k * m + j], A[piv * m + j]);
+            std::swap(b[k], b[piv]);
+        }
+        for (int i = k + 1; i < m; ++i) {
+            double f = A[i * m + k] / A[k * m + k];
+            for (int j = k; j < m; ++j) A[i * m + j] -= f * A[k * m + j];
+            b[i] -= f * b[k];
+        }
+    }
+    x.assign(m, 0.0);
+    for (int i = m - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < m; ++j) s -= A[i * m + j] * x[j];
+        x[i] = s / A[i * m + i];
+    }
+    return true;
+}
+
+extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem_kind, double* T1a,
+                                  double* T1b, double* T2aa, double* T2bb, double* T2ab, dcsd_result* res) {
+    if (!h || !o || !res) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    if ((o->ref != 0 && o->ref != 1) || (o->method != DCSD_CCSD && o->method != DCSD_DCSD) ||
+        (!valid_prec(o->precision) && o->precision != DCSD_PREC_MIXED) || o->maxiter < 1 ||
+        o->diis_n < 0 || o->diis_n > 16 || !(o->tol > 0.0) ||
+        (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
+        c->err = "invalid solve options";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    double* Tio[5] = {T1a, T1b, T2aa, T2bb, T2ab};
+    for (int k = 0; k < 5; ++k)
+        if (!Tio[k]) {
+            c->err = "NULL amplitude pointer";
+            return DCSD_ERR_INVALID_ARG;
+        }
+    auto t0 = std::chrono::steady_clock::now();
+    const int ref = o->ref;
+    const long len = 2l * c->O * c->V + 3l * c->O * c->O * c->V * c->V;
+    double* Td[5];
+    if (mem_kind == DCSD_MEM_HOST) {
+        DCSD_TRY(ensure_abi(c));
+        for (int k = 0; k < 5; ++k) Td[k] = c->abi[k];
+    } else {
+        for (int k = 0; k < 5; ++k) Td[k] = Tio[k];
+    }
+    if (o->use_guess) {
+        if (mem_kind == DCSD_MEM_HOST)
+            for (int k = 0; k < 5; ++k)
+                DCSD_CUDA(c, cudaMemcpyAsync(Td[k], Tio[k], abi_len(c, k) * sizeof(double),
+                                             cudaMemcpyHostToDevice, c->stream));
+        DCSD_TRY(unpack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]));
+    } else {
+        DCSD_CUDA(c, cudaMemsetAsync(c->t1, 0, len * sizeof(double), c->stream));
+    }
+    const int nd = o->diis_n;
+    if (nd > 0 && c->diis_cap < nd) {
+        if (c->diis_t) cudaFree(c->diis_t);
+        if (c->diis_e) cudaFree(c->diis_e);
+        c->diis_t = c->diis_e = nullptr;
+        c->diis_cap = 0;
+        DCSD_TRY(alloc(c, &c->diis_t, (size_t)nd * len));
+        DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
+        c->diis_cap = nd;
+    }
+    double* step = c->big0;  // scratch vectors (len <= ...) allocated separately below
+    double* tnew = nullptr;
+    std::vector<double> Bm(16 * 16, 0.0);
+    std::vector<int> slot_age;
+    int nhist = 0, next = 0;
+    bool switched = false;
+    int switched_at = -1;
+    const double* fa = c->fock[ref == 0 ? 0 : 1];
+    const double* fb = c->fock[ref == 0 ? 1 : 0];
+    double *sbuf = nullptr, *tbuf = nullptr;
+    if (nd == 0) {
+        DCSD_TRY(alloc(c, &sbuf, len));
+        DCSD_TRY(alloc(c, &tbuf, len));
+    }
+    dcsd_status status = DCSD_ERR_NOT_CONVERGED;
+    res->converged = 0;
+    res->switched_at = -1;
+    int it = 0;
+    for (it = 1; it <= o->maxiter; ++it) {
+        int prec = o->precision;
+        if (prec == DCSD_PREC_MIXED) prec = switched ? DCSD_PREC_BF16X3 : DCSD_PREC_BF16;
+        dcsd_status s = residual_union(c, ref, o->method, prec);
+        if (s != DCSD_OK) { status = s; break; }
+        if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
+        DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
+        if ((s = check_finite(c, c->R1, len, c->scal + 20)) != DCSD_OK) { status = s; break; }
+        if ((s = sync_scalars(c, 22)) != DCSD_OK) { status = s; break; }
+        const double W = c->hostbuf[0], dE = c->hostbuf[1], rmax = c->hostbuf[21];
+        res->W = W;
+        res->dEA = dE;
+        res->max_r = rmax;
+        if (c->hostbuf[20] != 0.0 || !std::isfinite(rmax)) {
+            c->err = "non-finite residual in solve";
+            status = DCSD_ERR_NUMERIC;
+            break;
+        }
+        if (rmax <= o->tol) {
+            status = DCSD_OK;
+            res->converged = 1;
+            break;
+        }
+        if (o->precision == DCSD_PREC_MIXED && !switched && rmax < o->switch_tol) {
+            switched = true;
+            switched_at = it;
+            nhist = 0;  // history built with the lower precision is discarded
+            next = 0;
+        }
+        if (it == o->maxiter) break;
+        double* st_v = nd > 0 ? c->diis_e + (size_t)next * len : sbuf;
+        double* tn_v = nd > 0 ? c->diis_t + (size_t)next * len : tbuf;
+        k_jacobi<<<grid_n(c, len), 256, 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, c->t1, c->R1,
+                                                        tn_v, st_v);
+        if ((s = launch_check(c, "jacobi")) != DCSD_OK) { status = s; break; }
+        if (nd == 0) {
+            DCSD_CUDA(c, cudaMemcpyAsync(c->t1, tn_v, len * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         c->stream));
+            continue;
+        }
+        const int cur = next;
+        next = (next + 1) % nd;
+        nhist = std::min(nhist + 1, nd);
+        // new row of the DIIS matrix
+        TV ev = view(st_v, {len});
+        for (int j = 0; j < nhist; ++j) {
+            int sl = (cur - j + nd) % nd;
+            if ((s = dot_view(c, ev, view(c->diis_e + (size_t)sl * len, {len}), c->scal + 24 + j, 0.0)) !=
+                DCSD_OK) { status = s; break; }
+        }
+        if (s != DCSD_OK) break;
+        DCSD_CUDA(c, cudaMemcpyAsync(c->hostbuf + 24, c->scal + 24, sizeof(double) * nhist,
+                                     cudaMemcpyDeviceToHost, c->stream));
+        DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int j = 0; j < nhist; ++j) {
+            int sl = (cur - j + nd) % nd;
+            Bm[cur * 16 + sl] = Bm[sl * 16 + cur] = c->hostbuf[24 + j];
+        }
+        LinComb lc;
+        lc.m = 0;
+        if (nhist >= 2) {
+            int m = nhist + 1;
+            std::vector<double> A(m * m, 0.0), bb(m, 0.0), xx;
+            std::vector<int> sl(nhist);
+            for (int j = 0; j < nhist; ++j) sl[j] = (cur - j + nd) % nd;
+            double scale = 0.0;
+            for (int a = 0; a < nhist; ++a) scale = std::max(scale, std::fabs(Bm[sl[a] * 16 + sl[a]]));
+            if (scale <= 0.0) scale = 1.0;
+            for (int a = 0; a < nhist; ++a)
+                for (int b = 0; b < nhist; ++b) A[a * m + b] = Bm[sl[a] * 16 + sl[b]] / scale;
+            for (int a = 0; a < nhist; ++a) { A[a * m + nhist] = -1.0; A[nhist * m + a] = -1.0; }
+            bb[nhist] = -1.0;
+            if (solve_small(m, A, bb, xx)) {
+                for (int j = 0; j < nhist; ++j) {
+                    lc.v[lc.m] = c->diis_t + (size_t)sl[j] * len;
+                    lc.coef[lc.m] = xx[j];
+                    lc.m++;
+                }
+            }
+        }
+        if (lc.m == 0) {
+            lc.v[0] = tn_v;
+            lc.coef[0] = 1.0;
+            lc.m = 1;
+        }
+        k_lincomb<<<grid_n(c, len), 256, 0, c->stream>>>(lc, len, c->t1);
+        if ((s = launch_check(c, "diis_extrapolate")) != DCSD_OK) { status = s; break; }
+    }
+    (void)step;
+    (void)tnew;
+    (void)slot_age;
+    if (sbuf) cudaFree(sbuf);
+    if (tbuf) cudaFree(tbuf);
+    res->iters = std::min(it, o->maxiter);
+    res->E_S = res->dEA + res->W;
+    res->E_T = res->dEA - res->W;
+    res->switched_at = switched_at;
+    // amplitudes out
+    dcsd_status ps = pack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]);
+    if (ps != DCSD_OK) return ps;
+    if (mem_kind == DCSD_MEM_HOST)
+        for (int k = 0; k < 5; ++k)
+            DCSD_CUDA(c, cudaMemcpyAsync(Tio[k], Td[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+    DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}

@@ -1,0 +1,197 @@
+// Internal declarations of the 2D-CCSD/2D-DCSD residual engine (not part of
+// the C ABI; see include/dcsd.h for the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dcsd.h"
+
+namespace dcsd {
+
+// ---------------------------------------------------------------------------
+// tensor views and contraction plans
+// ---------------------------------------------------------------------------
+constexpr int kMaxRank = 8;
+constexpr int kMaxMode = 4;
+
+// A strided view of a dense tensor: element (i0..i_{r-1}) lives at
+// p[sum_k i_k * stride[k]].  Index letters come from the einsum spec.
+struct TV {
+    double* p = nullptr;
+    int rank = 0;
+    long size[kMaxRank] = {};
+    long stride[kMaxRank] = {};
+};
+
+// Build a contiguous row-major view.
+TV view(double* p, std::initializer_list<long> sizes);
+// Sub-view: fix/offset/slice helpers operate on a copy.
+TV sub(TV v, int axis, long start, long len);   // range [start, start+len)
+TV fix(TV v, int axis, long at);                // drop axis at index 'at'
+TV perm(TV v, std::initializer_list<int> order);
+
+// A contraction C[batch, m, n] = alpha * sum_k A[batch, m, k] B[batch, n, k]
+// + beta * C, each of batch/m/n/k a product of up to kMaxMode strided modes.
+struct GemmPlan {
+    int nb = 0, nm = 0, nn = 0, nk = 0;
+    long b_size[kMaxMode], b_sa[kMaxMode], b_sb[kMaxMode], b_sc[kMaxMode];
+    long m_size[kMaxMode], m_sa[kMaxMode], m_sc[kMaxMode];
+    long n_size[kMaxMode], n_sb[kMaxMode], n_sc[kMaxMode];
+    long k_size[kMaxMode], k_sa[kMaxMode], k_sb[kMaxMode];
+    long NB = 1, M = 1, N = 1, K = 1;
+};
+
+// Parse "ab,bc->ac" style specs; returns false with a message on error.
+bool plan_einsum(const char* spec, const TV& A, const TV& B, const TV& C,
+                 GemmPlan& plan, std::string& err);
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct MTables;   // two-determinant coupling tables (mterm.cu)
+struct TcEngine;  // tensor-core contraction engine (tc_gemm.cu)
+
+struct Ctx {
+    int nc = 0, nv = 0, X = 0;
+    int n = 0, O = 0, V = 0;      // n = nc+2+nv; union occ O = nc+2; union vir V = nv+2
+    int o = 0, v = 0;             // per-spin ABI sizes
+    cudaStream_t stream = nullptr;
+    std::string err;
+    long long launches = 0;
+    int device = 0;
+    int num_sms = 0;
+
+    // inputs (device, FP64)
+    double* B = nullptr;          // [X][n][n]
+    double* fock[2] = {};         // Phi_A alpha / beta Fock [n][n]
+    double* Kref[2][2] = {};      // [ref][spin] exchange of the frame's occupied set [n][n]
+
+    // working tensors (device, FP64), union layout
+    double* t1 = nullptr;         // [2][O][V]
+    double* t2 = nullptr;         // [3][O][O][V][V] (aa, bb, ab)
+    double* R1 = nullptr;         // [2][O][V]
+    double* R2 = nullptr;         // [3][O][O][V][V]
+    double* Bd = nullptr;         // [2][X][n][n] T1-dressed DF factors
+    double* Pbt = nullptr;        // [X][n][O] scratch for dressing
+    double* fd = nullptr;         // [2][n][n] dressed Fock
+    double* fsc = nullptr;        // [8][n][n] small-matrix scratch
+    double* Z = nullptr;          // [2][X][O][V]
+    double* J = nullptr;          // [O][O][V][V] (kc|ld) (input-only, built at init)
+    double* H = nullptr;          // [3][O][O][O][O]
+    double* G = nullptr;          // [4][O][O][O][V] ladder T1 correction
+    double* Wo = nullptr;         // [O][O][O][O]
+    double* Foc = nullptr;        // [2][O][O]
+    double* Fvi = nullptr;        // [2][V][V]
+    double* big0 = nullptr;       // scratch >= max(ring matrices, ladder chunks)
+    double* big1 = nullptr;
+    double* big2 = nullptr;
+    double* big3 = nullptr;
+    size_t big_elems = 0;
+    double* abi[10] = {};         // device staging of ABI arrays for host mem_kind calls
+    double* red = nullptr;        // reduction scratch
+    double* scal = nullptr;       // device scalars: [0]=W [1]=dEA [2..] misc
+    double* c1 = nullptr;         // [2][O][V] two-determinant coefficients
+    double* hostbuf = nullptr;    // pinned host staging for scalars
+    int ladder_chunk = 8;         // virtual rows per V build chunk (FP64)
+
+    MTables* mt[2] = {};          // per reference
+    TcEngine* tc = nullptr;
+
+    // solver state (device)
+    double* diis_t = nullptr;     // [nd][len]
+    double* diis_e = nullptr;     // [nd][len]
+    int diis_cap = 0;
+};
+
+// error helpers
+#define DCSD_CUDA(ctx, call)                                                  \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);  \
+            return DCSD_ERR_CUDA;                                             \
+        }                                                                     \
+    } while (0)
+
+#define DCSD_TRY(call)                                                        \
+    do {                                                                      \
+        dcsd_status s_ = (call);                                              \
+        if (s_ != DCSD_OK) return s_;                                         \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// kernels (launchers return DCSD_OK or set ctx->err)
+// ---------------------------------------------------------------------------
+dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A,
+                     const TV& B, double beta, const TV& C);
+// C (+)= alpha * A elementwise over identical index sets (4D max), any strides
+dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& C);
+// sum_i A_i * B_i over identical shapes -> *out (device pointer), FP64
+dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accumulate);
+dcsd_status fill(Ctx* c, double* p, size_t n, double val);
+
+// layout conversion between the ABI and the union layout
+dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b,
+                     const double* T2aa, const double* T2bb, const double* T2ab);
+dcsd_status pack_R(Ctx* c, int ref, double* R1a, double* R1b, double* R2aa,
+                   double* R2bb, double* R2ab);
+dcsd_status pack_T(Ctx* c, int ref, double* T1a, double* T1b, double* T2aa,
+                   double* T2bb, double* T2ab);
+dcsd_status build_tau_mats(Ctx* c, int spin, double* Smat, double* Tmat);
+dcsd_status check_finite(Ctx* c, const double* p, size_t n, double* flag);
+
+// two-determinant layer
+dcsd_status mtables_build(Ctx* c);
+void mtables_free(Ctx* c);
+dcsd_status apply_mterms(Ctx* c, int ref);
+
+// residual orchestration (residual.cu)
+dcsd_status residual_union(Ctx* c, int ref, int method, int precision);
+dcsd_status init_constants(Ctx* c);
+
+// tensor-core engine (tc_gemm.cu)
+dcsd_status tc_init(Ctx* c);
+void tc_free(Ctx* c);
+// same contract as einsum64 with BF16 (nsplit=1) or split BF16 (nsplit=2,
+// three products) operands on tcgen05 tensor cores, FP32 accumulation
+dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A,
+                      const TV& B, double beta, const TV& C, int nsplit);
+
+// solver helpers (api.cu / solve kernels)
+dcsd_status jacobi_step(Ctx* c, int ref, double* step_out);
+
+inline dcsd_status launch_check(Ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return DCSD_ERR_CUDA;
+    }
+    c->launches++;
+    return DCSD_OK;
+}
+
+// frame description (which union positions are valid for each spin)
+struct Frame {
+    int occ_act[2];   // union occ index of the active occupied orbital per spin
+    int vir_act[2];   // union vir index of the active virtual orbital per spin
+};
+inline Frame frame_of(const Ctx* c, int ref) {
+    Frame f;
+    int t = c->nc, u = c->nc + 1;
+    if (ref == 0) {
+        f.occ_act[0] = t; f.occ_act[1] = u; f.vir_act[0] = 1; f.vir_act[1] = 0;
+    } else {
+        f.occ_act[0] = u; f.occ_act[1] = t; f.vir_act[0] = 0; f.vir_act[1] = 1;
+    }
+    return f;
+}
+
+}  // namespace dcsd
+
+struct dcsd_ctx {
+    dcsd::Ctx c;
+};

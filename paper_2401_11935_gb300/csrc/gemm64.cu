@@ -1,0 +1,607 @@
+// Strided FP64 contraction engine and elementwise kernels.
+//
+// Every tensor contraction of the residual is expressed as an einsum spec
+// over strided views (no explicit transposes): the planner classifies each
+// index letter as batch (A,B,C), m (A,C), n (B,C) or k (A,B), merges
+// adjacent modes and hands a GemmPlan to a shared-memory tiled FP64 kernel.
+// FP64 has no tcgen05 kind, so this path runs on the CUDA cores; it is the
+// parity path of the library and the fallback-free reference for the BF16
+// tensor-core engine (tc_gemm.cu) that shares the same planner.
+#include "common.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace dcsd {
+
+TV view(double* p, std::initializer_list<long> sizes) {
+    TV v;
+    v.p = p;
+    v.rank = (int)sizes.size();
+    int k = 0;
+    for (long s : sizes) v.size[k++] = s;
+    long st = 1;
+    for (int i = v.rank - 1; i >= 0; --i) {
+        v.stride[i] = st;
+        st *= v.size[i];
+    }
+    return v;
+}
+
+TV sub(TV v, int axis, long start, long len) {
+    v.p += start * v.stride[axis];
+    v.size[axis] = len;
+    return v;
+}
+
+TV fix(TV v, int axis, long at) {
+    TV r;
+    r.p = v.p + at * v.stride[axis];
+    r.rank = v.rank - 1;
+    int k = 0;
+    for (int i = 0; i < v.rank; ++i) {
+        if (i == axis) continue;
+        r.size[k] = v.size[i];
+        r.stride[k] = v.stride[i];
+        ++k;
+    }
+    return r;
+}
+
+TV perm(TV v, std::initializer_list<int> order) {
+    TV r = v;
+    int k = 0;
+    for (int a : order) {
+        r.size[k] = v.size[a];
+        r.stride[k] = v.stride[a];
+        ++k;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// einsum planner
+// ---------------------------------------------------------------------------
+namespace {
+struct Letter {
+    char ch;
+    long size;
+    long sa, sb, sc;
+    bool ina, inb, inc;
+};
+
+// merge adjacent modes (listed slow -> fast) when contiguous in every operand
+template <int NS>
+int merge_modes(int nmode, long* size, long* (&strides)[NS]) {
+    int w = 0;
+    for (int r = 0; r < nmode; ++r) {
+        if (size[r] == 1) continue;
+        if (w > 0) {
+            bool ok = true;
+            for (int s = 0; s < NS; ++s)
+                if (strides[s][w - 1] != strides[s][r] * size[r]) ok = false;
+            if (ok) {
+                size[w - 1] *= size[r];
+                for (int s = 0; s < NS; ++s) strides[s][w - 1] = strides[s][r];
+                continue;
+            }
+        }
+        size[w] = size[r];
+        for (int s = 0; s < NS; ++s) strides[s][w] = strides[s][r];
+        ++w;
+    }
+    return w;
+}
+}  // namespace
+
+bool plan_einsum(const char* spec, const TV& A, const TV& B, const TV& C,
+                 GemmPlan& P, std::string& err) {
+    std::string s(spec);
+    size_t comma = s.find(','), arrow = s.find("->");
+    if (comma == std::string::npos || arrow == std::string::npos || arrow < comma) {
+        err = "bad einsum spec " + s;
+        return false;
+    }
+    std::string sa = s.substr(0, comma), sb = s.substr(comma + 1, arrow - comma - 1),
+                sc = s.substr(arrow + 2);
+    if ((int)sa.size() != A.rank || (int)sb.size() != B.rank || (int)sc.size() != C.rank) {
+        err = "einsum rank mismatch for " + s;
+        return false;
+    }
+    std::vector<Letter> L;
+    auto find = [&](char ch) -> Letter* {
+        for (auto& l : L)
+            if (l.ch == ch) return &l;
+        L.push_back(Letter{ch, -1, 0, 0, 0, false, false, false});
+        return &L.back();
+    };
+    auto add = [&](const std::string& idx, const TV& t, int which) -> bool {
+        for (int i = 0; i < (int)idx.size(); ++i) {
+            Letter* l = find(idx[i]);
+            bool& in = which == 0 ? l->ina : which == 1 ? l->inb : l->inc;
+            if (in) {
+                err = "repeated index in one operand: " + s;
+                return false;
+            }
+            in = true;
+            if (l->size >= 0 && l->size != t.size[i]) {
+                err = "size mismatch for index " + std::string(1, idx[i]) + " in " + s;
+                return false;
+            }
+            l->size = t.size[i];
+            (which == 0 ? l->sa : which == 1 ? l->sb : l->sc) = t.stride[i];
+        }
+        return true;
+    };
+    if (!add(sa, A, 0) || !add(sb, B, 1) || !add(sc, C, 2)) return false;
+
+    long bsz[kMaxRank], bsa[kMaxRank], bsb[kMaxRank], bsc[kMaxRank];
+    long msz[kMaxRank], msa[kMaxRank], msc[kMaxRank];
+    long nsz[kMaxRank], nsb[kMaxRank], nsc[kMaxRank];
+    long ksz[kMaxRank], ksa[kMaxRank], ksb[kMaxRank];
+    int nb = 0, nm = 0, nn = 0, nk = 0;
+    // batch / m / n in C order; k in A order
+    for (char ch : sc) {
+        Letter* l = find(ch);
+        if (l->ina && l->inb) {
+            bsz[nb] = l->size; bsa[nb] = l->sa; bsb[nb] = l->sb; bsc[nb] = l->sc; ++nb;
+        } else if (l->ina) {
+            msz[nm] = l->size; msa[nm] = l->sa; msc[nm] = l->sc; ++nm;
+        } else if (l->inb) {
+            nsz[nn] = l->size; nsb[nn] = l->sb; nsc[nn] = l->sc; ++nn;
+        } else {
+            err = "output index absent from inputs in " + s;
+            return false;
+        }
+    }
+    for (char ch : sa) {
+        Letter* l = find(ch);
+        if (l->inc) continue;
+        if (!l->inb) {
+            err = "index summed in one operand only: " + s;
+            return false;
+        }
+        ksz[nk] = l->size; ksa[nk] = l->sa; ksb[nk] = l->sb; ++nk;
+    }
+    for (char ch : sb) {
+        Letter* l = find(ch);
+        if (!l->ina && !l->inc) {
+            err = "index summed in one operand only: " + s;
+            return false;
+        }
+    }
+    {
+        long* st[3] = {bsa, bsb, bsc};
+        nb = merge_modes<3>(nb, bsz, st);
+    }
+    {
+        long* st[2] = {msa, msc};
+        nm = merge_modes<2>(nm, msz, st);
+    }
+    {
+        long* st[2] = {nsb, nsc};
+        nn = merge_modes<2>(nn, nsz, st);
+    }
+    {
+        long* st[2] = {ksa, ksb};
+        nk = merge_modes<2>(nk, ksz, st);
+    }
+    if (nb > kMaxMode || nm > kMaxMode || nn > kMaxMode || nk > kMaxMode) {
+        err = "too many unmergeable modes in " + s;
+        return false;
+    }
+    P = GemmPlan();
+    P.nb = nb; P.nm = nm; P.nn = nn; P.nk = nk;
+    P.NB = P.M = P.N = P.K = 1;
+    for (int i = 0; i < nb; ++i) {
+        P.b_size[i] = bsz[i]; P.b_sa[i] = bsa[i]; P.b_sb[i] = bsb[i]; P.b_sc[i] = bsc[i];
+        P.NB *= bsz[i];
+    }
+    for (int i = 0; i < nm; ++i) {
+        P.m_size[i] = msz[i]; P.m_sa[i] = msa[i]; P.m_sc[i] = msc[i];
+        P.M *= msz[i];
+    }
+    for (int i = 0; i < nn; ++i) {
+        P.n_size[i] = nsz[i]; P.n_sb[i] = nsb[i]; P.n_sc[i] = nsc[i];
+        P.N *= nsz[i];
+    }
+    for (int i = 0; i < nk; ++i) {
+        P.k_size[i] = ksz[i]; P.k_sa[i] = ksa[i]; P.k_sb[i] = ksb[i];
+        P.K *= ksz[i];
+    }
+    for (auto& l : L)
+        if (l.size == 0) {
+            P.M = 0;  // empty contraction
+        }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tiled GEMM over a GemmPlan
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    const double* A;
+    const double* B;
+    double* C;
+    double alpha, beta;
+    GemmPlan p;
+    int a_kfast, b_kfast;
+};
+
+__device__ __forceinline__ void decomp2(long idx, int nmode, const long* size, const long* s1,
+                                        const long* s2, long& o1, long& o2) {
+    o1 = 0;
+    o2 = 0;
+#pragma unroll
+    for (int j = kMaxMode - 1; j >= 0; --j) {
+        if (j < nmode) {
+            long q = idx / size[j];
+            long r = idx - q * size[j];
+            o1 += r * s1[j];
+            o2 += r * s2[j];
+            idx = q;
+        }
+    }
+}
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
+    __shared__ double As[GBK][GBM + 1];
+    __shared__ double Bs[GBK][GBN + 1];
+    __shared__ long rA[GBM], rC[GBM], cB[GBN], cC[GBN];
+    __shared__ long kA[GBK], kB[GBK];
+    const GemmPlan& p = g.p;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long m0 = (long)blockIdx.x * GBM, n0 = (long)blockIdx.y * GBN;
+    for (long bz = blockIdx.z; bz < p.NB; bz += gridDim.z) {
+        long oA = 0, oB = 0, oC = 0;
+        {
+            long idx = bz;
+            for (int j = p.nb - 1; j >= 0; --j) {
+                long q = idx / p.b_size[j], r = idx - q * p.b_size[j];
+                oA += r * p.b_sa[j]; oB += r * p.b_sb[j]; oC += r * p.b_sc[j];
+                idx = q;
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < GBM; t += 256) {
+            long m = m0 + t;
+            if (m < p.M) decomp2(m, p.nm, p.m_size, p.m_sa, p.m_sc, rA[t], rC[t]);
+            else { rA[t] = -1; rC[t] = -1; }
+        }
+        for (int t = tid; t < GBN; t += 256) {
+            long n = n0 + t;
+            if (n < p.N) decomp2(n, p.nn, p.n_size, p.n_sb, p.n_sc, cB[t], cC[t]);
+            else { cB[t] = -1; cC[t] = -1; }
+        }
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (long k0 = 0; k0 < p.K; k0 += GBK) {
+            __syncthreads();
+            if (tid < GBK) {
+                long k = k0 + tid;
+                if (k < p.K) decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, kA[tid], kB[tid]);
+                else { kA[tid] = -1; kB[tid] = -1; }
+            }
+            __syncthreads();
+            for (int e = tid; e < GBM * GBK; e += 256) {
+                int mm, kk;
+                if (g.a_kfast) { kk = e % GBK; mm = e / GBK; }
+                else { mm = e % GBM; kk = e / GBM; }
+                long ra = rA[mm], ka = kA[kk];
+                As[kk][mm] = (ra >= 0 && ka >= 0) ? g.A[oA + ra + ka] : 0.0;
+            }
+            for (int e = tid; e < GBN * GBK; e += 256) {
+                int nn, kk;
+                if (g.b_kfast) { kk = e % GBK; nn = e / GBK; }
+                else { nn = e % GBN; kk = e / GBN; }
+                long cb = cB[nn], kb = kB[kk];
+                Bs[kk][nn] = (cb >= 0 && kb >= 0) ? g.B[oB + cb + kb] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GBK; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            long rc = rC[ty + 16 * i];
+            if (rc < 0) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                long cc = cC[tx + 16 * j];
+                if (cc < 0) continue;
+                double* cp = g.C + oC + rc + cc;
+                double v = g.alpha * acc[i][j];
+                if (g.beta != 0.0) v += g.beta * (*cp);
+                *cp = v;
+            }
+        }
+    }
+}
+
+dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
+                     double beta, const TV& C) {
+    GemmArgs g;
+    std::string err;
+    if (!plan_einsum(spec, A, B, C, g.p, err)) {
+        c->err = err;
+        return DCSD_ERR_INVALID_ARG;
+    }
+    if (g.p.M == 0 || g.p.N == 0 || g.p.NB == 0) return DCSD_OK;
+    g.A = A.p;
+    g.B = B.p;
+    g.C = C.p;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.a_kfast = (g.p.nk > 0 && g.p.k_sa[g.p.nk - 1] == 1) ? 1 : 0;
+    g.b_kfast = (g.p.nk > 0 && g.p.k_sb[g.p.nk - 1] == 1) ? 1 : 0;
+    dim3 grid((unsigned)((g.p.M + GBM - 1) / GBM), (unsigned)((g.p.N + GBN - 1) / GBN),
+              (unsigned)std::min<long>(g.p.NB, 65535));
+    k_gemm64<<<grid, 256, 0, c->stream>>>(g);
+    return launch_check(c, spec);
+}
+
+// ---------------------------------------------------------------------------
+// generic strided elementwise helpers (rank <= 6)
+// ---------------------------------------------------------------------------
+struct EwArgs {
+    int rank;
+    long size[6];
+    long sa[6], sc[6];
+    long total;
+    const double* A;
+    double* C;
+    double alpha, beta;
+};
+
+__global__ void k_axpy_view(EwArgs a) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.total;
+         e += (long)gridDim.x * blockDim.x) {
+        long idx = e, oa = 0, oc = 0;
+        for (int j = a.rank - 1; j >= 0; --j) {
+            long q = idx / a.size[j], r = idx - q * a.size[j];
+            oa += r * a.sa[j];
+            oc += r * a.sc[j];
+            idx = q;
+        }
+        double v = a.alpha * a.A[oa];
+        if (a.beta != 0.0) v += a.beta * a.C[oc];
+        a.C[oc] = v;
+    }
+}
+
+static bool ew_setup(Ctx* c, const TV& A, const TV& C, EwArgs& a) {
+    if (A.rank != C.rank || A.rank > 6) {
+        c->err = "elementwise view rank mismatch";
+        return false;
+    }
+    a.rank = A.rank;
+    a.total = 1;
+    for (int i = 0; i < A.rank; ++i) {
+        if (A.size[i] != C.size[i]) {
+            c->err = "elementwise view size mismatch";
+            return false;
+        }
+        a.size[i] = A.size[i];
+        a.sa[i] = A.stride[i];
+        a.sc[i] = C.stride[i];
+        a.total *= A.size[i];
+    }
+    return true;
+}
+
+static unsigned grid_for(Ctx* c, long total) {
+    long g = (total + 255) / 256;
+    long cap = (long)std::max(c->num_sms, 1) * 16;
+    return (unsigned)std::max<long>(1, std::min(g, cap));
+}
+
+dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& C) {
+    EwArgs a;
+    if (!ew_setup(c, A, C, a)) return DCSD_ERR_INVALID_ARG;
+    if (a.total == 0) return DCSD_OK;
+    a.A = A.p;
+    a.C = C.p;
+    a.alpha = alpha;
+    a.beta = beta;
+    k_axpy_view<<<grid_for(c, a.total), 256, 0, c->stream>>>(a);
+    return launch_check(c, "axpy_view");
+}
+
+// deterministic two-pass dot product
+constexpr int kDotBlocks = 512;
+
+__global__ void k_dot_partial(EwArgs a, const double* B, double* partial) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.total;
+         e += (long)gridDim.x * blockDim.x) {
+        long idx = e, oa = 0, ob = 0;
+        for (int j = a.rank - 1; j >= 0; --j) {
+            long q = idx / a.size[j], r = idx - q * a.size[j];
+            oa += r * a.sa[j];
+            ob += r * a.sc[j];
+            idx = q;
+        }
+        s = fma(a.A[oa], B[ob], s);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double* partial, int n, double* out, double accumulate) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += partial[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (accumulate != 0.0 ? *out : 0.0) + sh[0];
+}
+
+dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accumulate) {
+    EwArgs a;
+    if (!ew_setup(c, A, B, a)) return DCSD_ERR_INVALID_ARG;
+    a.A = A.p;
+    a.C = nullptr;
+    k_dot_partial<<<kDotBlocks, 256, 0, c->stream>>>(a, B.p, c->red);
+    DCSD_TRY(launch_check(c, "dot_partial"));
+    k_dot_final<<<1, 256, 0, c->stream>>>(c->red, kDotBlocks, out, accumulate);
+    return launch_check(c, "dot_final");
+}
+
+__global__ void k_fill(double* p, size_t n, double v) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        p[e] = v;
+}
+
+dcsd_status fill(Ctx* c, double* p, size_t n, double val) {
+    if (n == 0) return DCSD_OK;
+    k_fill<<<grid_for(c, (long)n), 256, 0, c->stream>>>(p, n, val);
+    return launch_check(c, "fill");
+}
+
+// ---------------------------------------------------------------------------
+// ABI <-> union layout
+// ---------------------------------------------------------------------------
+struct LayoutArgs {
+    int nc, o, v, O, V;
+    int occ_act[2], vir_act[2];
+};
+
+__device__ __forceinline__ int occ_map(const LayoutArgs& L, int s, int I) {
+    return I < L.nc ? I : L.occ_act[s];
+}
+__device__ __forceinline__ int vir_map(const LayoutArgs& L, int s, int A) {
+    return A == 0 ? L.vir_act[s] : A + 1;
+}
+
+// dir = 0: ABI -> union (scatter); dir = 1: union -> ABI (gather)
+__global__ void k_layout(LayoutArgs L, int dir, double* t1, double* t2, double* a1a, double* a1b,
+                         double* a2aa, double* a2bb, double* a2ab) {
+    const long n1 = (long)L.o * L.v, n2 = (long)L.o * L.o * L.v * L.v;
+    const long total = 2 * n1 + 3 * n2;
+    const long O = L.O, V = L.V;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        if (e < 2 * n1) {
+            int s = (int)(e / n1);
+            long r = e - s * n1;
+            int I = (int)(r / L.v), A = (int)(r % L.v);
+            double* abi = (s == 0 ? a1a : a1b) + r;
+            double* un = t1 + ((long)s * O + occ_map(L, s, I)) * V + vir_map(L, s, A);
+            if (dir == 0) *un = *abi; else *abi = *un;
+        } else {
+            long r = e - 2 * n1;
+            int blk = (int)(r / n2);
+            r -= blk * n2;
+            int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+            int b = (int)(r % L.v);
+            long q = r / L.v;
+            int a = (int)(q % L.v);
+            q /= L.v;
+            int j = (int)(q % L.o);
+            int i = (int)(q / L.o);
+            double* abi = (blk == 0 ? a2aa : blk == 1 ? a2bb : a2ab) + r;
+            long ui = occ_map(L, s1, i), uj = occ_map(L, s2, j);
+            long ua = vir_map(L, s1, a), ub = vir_map(L, s2, b);
+            double* un = t2 + (((blk * O + ui) * O + uj) * V + ua) * V + ub;
+            if (dir == 0) *un = *abi; else *abi = *un;
+        }
+    }
+}
+
+static LayoutArgs layout_args(Ctx* c, int ref) {
+    LayoutArgs L;
+    L.nc = c->nc; L.o = c->o; L.v = c->v; L.O = c->O; L.V = c->V;
+    Frame f = frame_of(c, ref);
+    for (int s = 0; s < 2; ++s) { L.occ_act[s] = f.occ_act[s]; L.vir_act[s] = f.vir_act[s]; }
+    return L;
+}
+
+dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b, const double* T2aa,
+                     const double* T2bb, const double* T2ab) {
+    size_t n1 = 2ul * c->O * c->V, n2 = 3ul * c->O * c->O * c->V * c->V;
+    DCSD_CUDA(c, cudaMemsetAsync(c->t1, 0, n1 * sizeof(double), c->stream));
+    DCSD_CUDA(c, cudaMemsetAsync(c->t2, 0, n2 * sizeof(double), c->stream));
+    LayoutArgs L = layout_args(c, ref);
+    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
+    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 0, c->t1, c->t2, (double*)T1a,
+                                                          (double*)T1b, (double*)T2aa,
+                                                          (double*)T2bb, (double*)T2ab);
+    return launch_check(c, "unpack_T");
+}
+
+dcsd_status pack_R(Ctx* c, int ref, double* R1a, double* R1b, double* R2aa, double* R2bb,
+                   double* R2ab) {
+    LayoutArgs L = layout_args(c, ref);
+    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
+    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 1, c->R1, c->R2, R1a, R1b, R2aa,
+                                                          R2bb, R2ab);
+    return launch_check(c, "pack_R");
+}
+
+dcsd_status pack_T(Ctx* c, int ref, double* T1a, double* T1b, double* T2aa, double* T2bb,
+                   double* T2ab) {
+    LayoutArgs L = layout_args(c, ref);
+    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
+    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 1, c->t1, c->t2, T1a, T1b, T2aa,
+                                                          T2bb, T2ab);
+    return launch_check(c, "pack_T");
+}
+
+// S = 1 - tau, T = 1 + tau with tau[nc + a][k] = t1[spin][k][a]
+__global__ void k_tau_mats(int n, int nc, int O, int V, const double* t1s, double* S, double* T) {
+    long total = (long)n * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        int p = (int)(e / n), q = (int)(e % n);
+        double tau = 0.0;
+        if (p >= nc && q < O) tau = t1s[(long)q * V + (p - nc)];
+        double d = p == q ? 1.0 : 0.0;
+        S[e] = d - tau;
+        T[e] = d + tau;
+    }
+}
+
+dcsd_status build_tau_mats(Ctx* c, int spin, double* Smat, double* Tmat) {
+    k_tau_mats<<<grid_for(c, (long)c->n * c->n), 256, 0, c->stream>>>(
+        c->n, c->nc, c->O, c->V, c->t1 + (long)spin * c->O * c->V, Smat, Tmat);
+    return launch_check(c, "tau_mats");
+}
+
+__global__ void k_finite(const double* p, size_t n, double* flag) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(p[e])) *flag = 1.0;
+}
+
+dcsd_status check_finite(Ctx* c, const double* p, size_t n, double* flag) {
+    k_finite<<<grid_for(c, (long)n), 256, 0, c->stream>>>(p, n, flag);
+    return launch_check(c, "check_finite");
+}
+
+}  // namespace dcsd

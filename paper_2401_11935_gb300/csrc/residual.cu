@@ -1,0 +1,306 @@
+// One evaluation of the 2D-CCSD / 2D-DCSD residual on the GPU.
+//
+// Paper: arXiv 2401.11935, Section II, Eqs. 2-4.  The single-reference part
+// R^X (CCSD or DCSD) is evaluated in the T1-similarity-transformed
+// ("dressed") Hamiltonian, where the CCSD doubles take the form of the CCD
+// doubles with dressed integrals and the singles need only T2 and dressed
+// quantities:
+//   Bd^s = (1 - tau^s) B (1 + tau^s)          tau^s[vir a][occ k] = t1^s[k][a]
+//   fd^s = (1 - tau^s)(f^s + K^s + J(t1))(1 + tau^s) - Kd^s
+// Layout: every amplitude/residual block lives on the spin-free "union"
+// index spaces occ' = (core, t, u), vir' = (t, u, V), zero-padded where an
+// orbital does not belong to the spin's space.  All integrals are then
+// spin-free spatial quantities and the three doubles blocks (aa, bb, ab) are
+// stacked rows of one matrix -- the particle-particle ladder uses one
+// undressed (ac|bd) for all three blocks, plus explicit T1 corrections.
+//
+// DC (Section II: DC applied to the doubles "in the usual way"): the
+// exchange part of the quadratic ring is dropped (x = 0) and the two
+// Fock-like quadratic terms are halved (y = 1/2); CCSD has x = y = 1.
+#include "common.h"
+
+namespace dcsd {
+
+namespace {
+
+struct Views {
+    long n, nc, O, V, X;
+    TV B, Bov, Bvv, t1, t2, R1, R2, Bd, Z, J;
+};
+
+TV blk(const TV& v, int b) { return fix(v, 0, b); }
+
+}  // namespace
+
+dcsd_status init_constants(Ctx* c) {
+    const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
+    TV B = view(c->B, {X, n, n});
+    TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
+    DCSD_TRY(einsum64(c, "Lkc,Lld->klcd", 1.0, Bov, Bov, 0.0, view(c->J, {O, O, V, V})));
+    for (int ref = 0; ref < 2; ++ref) {
+        Frame f = frame_of(c, ref);
+        for (int s = 0; s < 2; ++s) {
+            TV K = view(c->Kref[ref][s], {n, n});
+            double beta = 0.0;
+            if (nc > 0) {
+                DCSD_TRY(einsum64(c, "Lpk,Lkq->pq", 1.0, sub(B, 2, 0, nc), sub(B, 1, 0, nc), 0.0, K));
+                beta = 1.0;
+            }
+            DCSD_TRY(einsum64(c, "Lp,Lq->pq", 1.0, fix(B, 2, f.occ_act[s]), fix(B, 1, f.occ_act[s]),
+                              beta, K));
+        }
+    }
+    return DCSD_OK;
+}
+
+__global__ void k_energy_combine(double* s) {
+    // s[1] = f.t1 ; s[2..4] = J.t2 (aa, bb, ab); s[5..6] direct/exchange t1 t1 (aa);
+    // s[7..8] (bb); s[9] ab direct
+    s[1] = s[1] + 0.5 * (s[2] + s[5] - s[6] + s[3] + s[7] - s[8]) + s[4] + s[9];
+}
+
+dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
+    const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
+    const double x = method == DCSD_CCSD ? 1.0 : 0.0;
+    const double y = method == DCSD_CCSD ? 1.0 : 0.5;
+    const Frame fr = frame_of(c, ref);
+    const int nsplit = prec == DCSD_PREC_BF16X3 ? 2 : 1;
+    auto big = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
+                   const TV& C) -> dcsd_status {
+        if (prec == DCSD_PREC_FP64) return einsum64(c, spec, alpha, A, Bm, beta, C);
+        return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
+    };
+    auto sml = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
+                   const TV& C) -> dcsd_status { return einsum64(c, spec, alpha, A, Bm, beta, C); };
+
+    TV B = view(c->B, {X, n, n});
+    TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
+    TV Bvv = sub(sub(B, 1, nc, V), 2, nc, V);
+    TV t1 = view(c->t1, {2, O, V});
+    TV t2 = view(c->t2, {3, O, O, V, V});
+    TV R1 = view(c->R1, {2, O, V});
+    TV R2 = view(c->R2, {3, O, O, V, V});
+    TV Bd = view(c->Bd, {2, X, n, n});
+    TV Z = view(c->Z, {2, X, O, V});
+    TV J = view(c->J, {O, O, V, V});
+    TV fd = view(c->fd, {2, n, n});
+    auto BdVO = [&](int s) { return sub(sub(blk(Bd, s), 1, nc, V), 2, 0, O); };  // [L][a][i]
+    auto BdOO = [&](int s) { return sub(sub(blk(Bd, s), 1, 0, O), 2, 0, O); };  // [L][k][i]
+    auto BdVV = [&](int s) { return sub(sub(blk(Bd, s), 1, nc, V), 2, nc, V); };  // [L][a][c]
+    const double* fock_s[2] = {c->fock[ref == 0 ? 0 : 1], c->fock[ref == 0 ? 1 : 0]};
+    const size_t nn2 = (size_t)n * n;
+
+    // ---- T1 dressing of the DF factors -----------------------------------
+    for (int s = 0; s < 2; ++s) {
+        TV t1s = blk(t1, s);
+        TV P = view(c->Pbt, {X, n, O});
+        DCSD_TRY(sml("Lpa,ka->Lpk", 1.0, sub(B, 2, nc, V), t1s, 0.0, P));
+        TV Bds = blk(Bd, s);
+        DCSD_CUDA(c, cudaMemcpyAsync(Bds.p, c->B, sizeof(double) * X * nn2, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        DCSD_TRY(axpy_view(c, 1.0, P, 1.0, sub(Bds, 2, 0, O)));
+        DCSD_TRY(sml("ka,Lkq->Laq", -1.0, t1s, sub(B, 1, 0, O), 1.0, sub(Bds, 1, nc, V)));
+        DCSD_TRY(sml("ka,Lkm->Lam", -1.0, t1s, sub(P, 1, 0, O), 1.0, sub(sub(Bds, 1, nc, V), 2, 0, O)));
+    }
+
+    // ---- dressed Fock matrices -------------------------------------------
+    {
+        TV jv = view(c->fsc + 7 * nn2, {X});
+        TV Bova = sub(sub(B, 1, 0, O), 2, nc, V);
+        DCSD_TRY(sml("Lka,ka->L", 1.0, Bova, blk(t1, 0), 0.0, jv));
+        DCSD_TRY(sml("Lka,ka->L", 1.0, Bova, blk(t1, 1), 1.0, jv));
+        TV Jt = view(c->fsc, {n, n});
+        DCSD_TRY(sml("Lpq,L->pq", 1.0, B, jv, 0.0, Jt));
+        for (int s = 0; s < 2; ++s) {
+            TV F1 = view(c->fsc + 1 * nn2, {n, n});
+            DCSD_CUDA(c, cudaMemcpyAsync(F1.p, fock_s[s], sizeof(double) * nn2, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+            DCSD_TRY(axpy_view(c, 1.0, view(c->Kref[ref][s], {n, n}), 1.0, F1));
+            DCSD_TRY(axpy_view(c, 1.0, Jt, 1.0, F1));
+            TV S = view(c->fsc + 2 * nn2, {n, n}), Tm = view(c->fsc + 3 * nn2, {n, n});
+            DCSD_TRY(build_tau_mats(c, s, S.p, Tm.p));
+            TV tmp = view(c->fsc + 4 * nn2, {n, n});
+            DCSD_TRY(sml("pr,rq->pq", 1.0, F1, Tm, 0.0, tmp));
+            TV fds = blk(fd, s);
+            DCSD_TRY(sml("pr,rq->pq", 1.0, S, tmp, 0.0, fds));
+            TV Bds = blk(Bd, s);
+            if (nc > 0)
+                DCSD_TRY(sml("Lpk,Lkq->pq", -1.0, sub(Bds, 2, 0, nc), sub(Bds, 1, 0, nc), 1.0, fds));
+            DCSD_TRY(sml("Lp,Lq->pq", -1.0, fix(Bds, 2, fr.occ_act[s]), fix(Bds, 1, fr.occ_act[s]), 1.0,
+                         fds));
+        }
+    }
+
+    // ---- Z^s_L[i][a] = sum_{kc} T^{s.}[(ia),(kc)] B_L[k][c] ------------------
+    DCSD_TRY(big("ikac,Lkc->Lia", 1.0, blk(t2, 0), Bov, 0.0, blk(Z, 0)));
+    DCSD_TRY(big("ikac,Lkc->Lia", 1.0, blk(t2, 2), Bov, 1.0, blk(Z, 0)));
+    DCSD_TRY(big("ikac,Lkc->Lia", 1.0, blk(t2, 1), Bov, 0.0, blk(Z, 1)));
+    DCSD_TRY(big("kica,Lkc->Lia", 1.0, blk(t2, 2), Bov, 1.0, blk(Z, 1)));
+
+    DCSD_CUDA(c, cudaMemsetAsync(c->R2, 0, sizeof(double) * 3 * O * O * V * V, c->stream));
+    const int s1_of[3] = {0, 1, 0}, s2_of[3] = {0, 1, 1};
+
+    // ---- <ab||ij> (dressed) -------------------------------------------------
+    for (int b = 0; b < 3; ++b) {
+        int s1 = s1_of[b], s2 = s2_of[b];
+        DCSD_TRY(big("Lai,Lbj->ijab", 1.0, BdVO(s1), BdVO(s2), 1.0, blk(R2, b)));
+        if (s1 == s2) DCSD_TRY(big("Laj,Lbi->ijab", -1.0, BdVO(s1), BdVO(s1), 1.0, blk(R2, b)));
+    }
+
+    // ---- Fock terms incl. the Fock-like quadratic terms ---------------------
+    TV Foc = view(c->Foc, {2, O, O}), Fvi = view(c->Fvi, {2, V, V});
+    for (int s = 0; s < 2; ++s) {
+        TV fds = blk(fd, s);
+        DCSD_TRY(sml("Lme,Lje->mj", y, Bov, blk(Z, s), 0.0, blk(Foc, s)));
+        DCSD_TRY(axpy_view(c, 1.0, sub(sub(fds, 0, 0, O), 1, 0, O), 1.0, blk(Foc, s)));
+        DCSD_TRY(sml("Lme,Lmb->be", -y, Bov, blk(Z, s), 0.0, blk(Fvi, s)));
+        DCSD_TRY(axpy_view(c, 1.0, sub(sub(fds, 0, nc, V), 1, nc, V), 1.0, blk(Fvi, s)));
+    }
+    for (int b = 0; b < 3; ++b) {
+        int s1 = s1_of[b], s2 = s2_of[b];
+        DCSD_TRY(big("bc,ijac->ijab", 1.0, blk(Fvi, s2), blk(t2, b), 1.0, blk(R2, b)));
+        DCSD_TRY(big("ac,ijcb->ijab", 1.0, blk(Fvi, s1), blk(t2, b), 1.0, blk(R2, b)));
+        DCSD_TRY(big("kj,ikab->ijab", -1.0, blk(Foc, s2), blk(t2, b), 1.0, blk(R2, b)));
+        DCSD_TRY(big("ki,kjab->ijab", -1.0, blk(Foc, s1), blk(t2, b), 1.0, blk(R2, b)));
+    }
+
+    // ---- particle-particle ladder (undressed (ac|bd), stacked blocks) --------
+    {
+        long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
+        for (long a0 = 0; a0 < V; a0 += ch) {
+            long na = std::min(ch, V - a0);
+            TV Vc = view(c->big0, {na, V, V, V});  // [a][c][b][d] = (ac|bd)
+            DCSD_TRY(big("Lac,Lbd->acbd", 1.0, sub(Bvv, 1, a0, na), Bvv, 0.0, Vc));
+            DCSD_TRY(big("sijcd,acbd->sijab", 1.0, t2, Vc, 1.0, sub(R2, 3, a0, na)));
+        }
+    }
+    // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with t_ab
+    // transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
+    TV G = view(c->G, {4, O, O, O, V});
+    TV H = view(c->H, {3, O, O, O, O});
+    {
+        long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
+        for (long k0 = 0; k0 < O; k0 += kc) {
+            long nk = std::min(kc, O - k0);
+            TV Ic = view(c->big0, {nk, V, V, V});  // [k][c][b][d]
+            DCSD_TRY(big("Lkc,Lbd->kcbd", 1.0, sub(Bov, 1, k0, nk), Bvv, 0.0, Ic));
+            DCSD_TRY(big("sijcd,kcbd->sijkb", 1.0, t2, Ic, 0.0, sub(sub(G, 0, 0, 3), 3, k0, nk)));
+            DCSD_TRY(big("ijdc,kcbd->ijkb", 1.0, blk(t2, 2), Ic, 0.0, sub(blk(G, 3), 2, k0, nk)));
+        }
+    }
+    DCSD_TRY(big("kmcd,sijcd->sijkm", 1.0, J, t2, 0.0, H));
+    for (int b = 0; b < 3; ++b) {
+        int s1 = s1_of[b], s2 = s2_of[b];
+        DCSD_TRY(sml("ka,ijkb->ijab", -1.0, blk(t1, s1), blk(G, b), 1.0, blk(R2, b)));
+        if (s1 == s2) DCSD_TRY(sml("mb,ijma->ijab", 1.0, blk(t1, s2), blk(G, b), 1.0, blk(R2, b)));
+        else DCSD_TRY(sml("mb,ijma->ijab", -1.0, blk(t1, s2), blk(G, 3), 1.0, blk(R2, b)));
+        TV tmp = view(c->big1, {O, O, O, V});
+        DCSD_TRY(sml("ijkm,mb->ijkb", 1.0, blk(H, b), blk(t1, s2), 0.0, tmp));
+        DCSD_TRY(sml("ka,ijkb->ijab", 1.0, blk(t1, s1), tmp, 1.0, blk(R2, b)));
+    }
+
+    // ---- hole-hole ladder with the quadratic ladder term --------------------
+    for (int b = 0; b < 3; ++b) {
+        int s1 = s1_of[b], s2 = s2_of[b];
+        double cs = s1 == s2 ? 0.5 : 1.0;
+        TV Wo = view(c->Wo, {O, O, O, O});
+        DCSD_TRY(sml("Lki,Llj->klij", 1.0, BdOO(s1), BdOO(s2), 0.0, Wo));
+        DCSD_TRY(axpy_view(c, cs, perm(blk(H, b), {2, 3, 0, 1}), 1.0, Wo));
+        DCSD_TRY(big("klij,klab->ijab", 1.0, Wo, blk(t2, b), 1.0, blk(R2, b)));
+    }
+
+    // ---- ring (particle-hole) terms ------------------------------------------
+    {
+        TV Uex[2] = {view(c->big0, {O, V, O, V}), view(c->big1, {O, V, O, V})};  // (kj|bc) as [k][c][j][b]
+        for (int s = 0; s < 2; ++s) DCSD_TRY(big("Lkj,Lbc->kcjb", 1.0, BdOO(s), BdVV(s), 0.0, Uex[s]));
+        TV Kq = perm(J, {0, 1, 3, 2});  // [k][l][c][d] = (kd|lc)
+        auto Tm = [&](int sg, int tg) -> TV {
+            if (sg == tg) return blk(t2, sg);
+            if (sg == 0) return blk(t2, 2);
+            return perm(blk(t2, 2), {1, 0, 3, 2});
+        };
+        TV Xacc = view(c->big2, {O, V, O, V});
+        TV scr = view(c->big3, {O, V, O, V});
+        for (int sg = 0; sg < 2; ++sg)
+            for (int sp = 0; sp < 2; ++sp) {
+                TV Ycol = view(c->big3, {X, O, V});
+                DCSD_TRY(axpy_view(c, 1.0, perm(BdVO(sp), {0, 2, 1}), 0.0, Ycol));
+                DCSD_TRY(axpy_view(c, 0.5, blk(Z, sp), 1.0, Ycol));
+                DCSD_TRY(big("Lia,Ljb->iajb", 1.0, blk(Z, sg), Ycol, 0.0, Xacc));
+                for (int tg = 0; tg < 2; ++tg) {
+                    if (tg == sp) DCSD_TRY(big("ikac,kcjb->iajb", -1.0, Tm(sg, tg), Uex[tg], 1.0, Xacc));
+                    if (x != 0.0) {
+                        DCSD_TRY(big("klcd,jlbd->kcjb", 1.0, Kq, Tm(sp, tg), 0.0, scr));
+                        DCSD_TRY(big("ikac,kcjb->iajb", -0.5 * x, Tm(sg, tg), scr, 1.0, Xacc));
+                    }
+                }
+                if (sg == sp) {
+                    TV R = blk(R2, sg);
+                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {0, 2, 1, 3}), 1.0, R));
+                    DCSD_TRY(axpy_view(c, -1.0, perm(Xacc, {2, 0, 1, 3}), 1.0, R));
+                    DCSD_TRY(axpy_view(c, -1.0, perm(Xacc, {0, 2, 3, 1}), 1.0, R));
+                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {2, 0, 3, 1}), 1.0, R));
+                } else if (sg == 0) {
+                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {0, 2, 1, 3}), 1.0, blk(R2, 2)));
+                } else {
+                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {2, 0, 3, 1}), 1.0, blk(R2, 2)));
+                }
+            }
+        // mixed-spin pairs of the alpha-beta block
+        TV M1 = view(c->big0, {O, V, O, V});  // [k][c][i][b]
+        DCSD_TRY(big("Lki,Lbc->kcib", -1.0, BdOO(0), BdVV(1), 0.0, M1));
+        if (x != 0.0) DCSD_TRY(big("kldc,ildb->kcib", 0.5 * x, J, blk(t2, 2), 1.0, M1));
+        DCSD_TRY(big("kjac,kcib->ijab", 1.0, blk(t2, 2), M1, 1.0, blk(R2, 2)));
+        TV M2 = view(c->big1, {O, V, O, V});  // [k][c][j][a]
+        DCSD_TRY(big("Lkj,Lac->kcja", -1.0, BdOO(1), BdVV(0), 0.0, M2));
+        if (x != 0.0) DCSD_TRY(big("kldc,ljad->kcja", 0.5 * x, J, blk(t2, 2), 1.0, M2));
+        DCSD_TRY(big("ikcb,kcja->ijab", 1.0, blk(t2, 2), M2, 1.0, blk(R2, 2)));
+    }
+
+    // ---- singles ---------------------------------------------------------------
+    for (int s = 0; s < 2; ++s) {
+        TV fds = blk(fd, s);
+        DCSD_TRY(axpy_view(c, 1.0, perm(sub(sub(fds, 0, nc, V), 1, 0, O), {1, 0}), 0.0, blk(R1, s)));
+        DCSD_TRY(sml("Lac,Lic->ia", 1.0, BdVV(s), blk(Z, s), 1.0, blk(R1, s)));
+        DCSD_TRY(sml("Lki,Lka->ia", -1.0, BdOO(s), blk(Z, s), 1.0, blk(R1, s)));
+    }
+    {
+        auto fdOV = [&](int s) { return sub(sub(blk(fd, s), 0, 0, O), 1, nc, V); };
+        DCSD_TRY(sml("kc,ikac->ia", 1.0, fdOV(0), blk(t2, 0), 1.0, blk(R1, 0)));
+        DCSD_TRY(sml("kc,ikac->ia", 1.0, fdOV(1), blk(t2, 2), 1.0, blk(R1, 0)));
+        DCSD_TRY(sml("kc,ikac->ia", 1.0, fdOV(1), blk(t2, 1), 1.0, blk(R1, 1)));
+        DCSD_TRY(sml("kc,kica->ia", 1.0, fdOV(0), blk(t2, 2), 1.0, blk(R1, 1)));
+    }
+
+    // ---- energy Delta E_A (Eq. 2) ----------------------------------------------
+    {
+        double* s = c->scal;
+        for (int sp = 0; sp < 2; ++sp) {
+            TV fo = sub(sub(view((double*)fock_s[sp], {n, n}), 0, 0, O), 1, nc, V);
+            DCSD_TRY(dot_view(c, fo, blk(t1, sp), s + 1, sp == 0 ? 0.0 : 1.0));
+        }
+        for (int b = 0; b < 3; ++b) DCSD_TRY(dot_view(c, J, blk(t2, b), s + 2 + b, 0.0));
+        TV u = view(c->fsc + 5 * nn2, {O, V});
+        for (int sp = 0; sp < 2; ++sp) {
+            DCSD_TRY(sml("ijab,jb->ia", 1.0, J, blk(t1, sp), 0.0, u));
+            DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 5 + 2 * sp, 0.0));
+            DCSD_TRY(sml("ijab,ja->ib", 1.0, J, blk(t1, sp), 0.0, u));
+            DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 6 + 2 * sp, 0.0));
+        }
+        DCSD_TRY(sml("ijab,jb->ia", 1.0, J, blk(t1, 1), 0.0, u));
+        DCSD_TRY(dot_view(c, u, blk(t1, 0), s + 9, 0.0));
+        k_energy_combine<<<1, 1, 0, c->stream>>>(s);
+        DCSD_TRY(launch_check(c, "energy_combine"));
+    }
+
+    // ---- W = R^X at the A->B double; two-determinant terms ------------------------
+    {
+        long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
+        DCSD_CUDA(c, cudaMemcpyAsync(c->scal, c->R2 + e, sizeof(double), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    }
+    DCSD_TRY(apply_mterms(c, ref));
+    return DCSD_OK;
+}
+
+}  // namespace dcsd
