@@ -67,8 +67,9 @@ typedef enum { DCSD_MEM_HOST = 0, DCSD_MEM_DEVICE = 1 } dcsd_mem_kind;
 typedef enum {
     DCSD_PREC_FP64 = 0,   /* FP64 on CUDA cores                              */
     DCSD_PREC_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 acc */
-    DCSD_PREC_BF16X3 = 2, /* split operands hi+lo, 3 BF16 products (FP32x2)  */
-    DCSD_PREC_MIXED = 3   /* dcsd_solve only: BF16, then BF16X3 below switch */
+    DCSD_PREC_BF16X3 = 2, /* split operands hi+mid, 3 BF16 products          */
+    DCSD_PREC_MIXED = 3,  /* dcsd_solve only: BF16, then BF16X6 (see below)  */
+    DCSD_PREC_BF16X6 = 4  /* split hi+mid+lo, 6 BF16 products (FP32-class)  */
 } dcsd_precision;
 
 typedef struct dcsd_ctx dcsd_ctx;
@@ -86,7 +87,8 @@ typedef struct {
     int maxiter;        /* iteration cap (e.g. 100)                         */
     int diis_n;         /* DIIS history length, 0..16 (0 = Jacobi only)     */
     double tol;         /* convergence: max |R| <= tol                      */
-    double switch_tol;  /* MIXED: switch BF16 -> BF16X3 when max|R| < this  */
+    double switch_tol;  /* MIXED: switch BF16 -> BF16X6 when max|R| < this, or
+                           when max|R| has not halved in 6 iterations      */
     int use_guess;      /* 1: start from the T passed in, 0: from T = 0      */
 } dcsd_solve_opts;
 
@@ -129,7 +131,7 @@ dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const double* eps,
  *   synchronises the stream) or device pointers (asynchronous on the
  *   context stream; W and dEA are still host doubles and the call
  *   synchronises before returning them).  Outputs may not alias inputs.
- *   precision: DCSD_PREC_FP64, _BF16 or _BF16X3.
+ *   precision: DCSD_PREC_FP64, _BF16, _BF16X3 or _BF16X6.
  * Errors: INVALID_ARG, CUDA, NUMERIC (NaN/Inf in R). */
 dcsd_status dcsd_residual(dcsd_ctx* ctx, int ref, int method, int precision,
                           int mem_kind,
@@ -152,7 +154,10 @@ dcsd_status dcsd_energy(dcsd_ctx* ctx, int ref, int method, int mem_kind,
  * steps with Fock-diagonal denominators + Pulay DIIS, all FP64 vector
  * algebra on the device).  T* are in/out (initial guess if
  * opts->use_guess, converged amplitudes on return), mem_kind as above.
- * Returns NOT_CONVERGED (with T and *res filled) if maxiter is reached. */
+ * Every iteration is one residual evaluation followed by one update; the
+ * loop stops before the update once max|R| <= tol.  Returns NOT_CONVERGED
+ * if maxiter is reached (T then holds the amplitudes after the last update,
+ * *res the figures of the last residual). */
 dcsd_status dcsd_solve(dcsd_ctx* ctx, const dcsd_solve_opts* opts, int mem_kind,
                        double* T1a, double* T1b, double* T2aa, double* T2bb,
                        double* T2ab, dcsd_result* res);
@@ -174,6 +179,27 @@ const char* dcsd_last_error(const dcsd_ctx* ctx);
 /* dcsd_kernel_launches -- number of kernels this context has launched since
  * creation (diagnostics / benchmark accounting). */
 long long dcsd_kernel_launches(const dcsd_ctx* ctx);
+
+/* Kernel classes reported by dcsd_profile. */
+typedef enum {
+    DCSD_PROF_LADDER = 0,   /* tcgen05 GEMMs of the particle-particle ladder    */
+    DCSD_PROF_TC_OTHER = 1, /* other tcgen05 GEMMs (ring, DF builds, ...)       */
+    DCSD_PROF_PACK = 2,     /* BF16 operand packing                             */
+    DCSD_PROF_FP64 = 3,     /* FP64 CUDA-core contractions                      */
+    DCSD_PROF_NCLASS = 8
+} dcsd_prof_class;
+
+/* dcsd_profile -- device-time accounting of the context's kernels, measured
+ * with CUDA events recorded on the context stream around every launch of
+ * the classes above while enabled.
+ *   enable : 1 start/continue recording, 0 stop.
+ *   reset  : 1 clears the accumulated figures before (re)enabling.
+ *   ms, launches : if non-NULL, arrays of DCSD_PROF_NCLASS receiving the
+ *            summed device milliseconds and launch counts per class since
+ *            the last reset (the call synchronises the stream to read them).
+ * Errors: INVALID_ARG (NULL ctx), CUDA. */
+dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
+                         long long* launches);
 
 #ifdef __cplusplus
 }

@@ -10,10 +10,10 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib as L
-from ._lib import (CCSD, DCSD, MEM_DEVICE, MEM_HOST, PREC_BF16, PREC_BF16X3, PREC_FP64,  # noqa: F401
-                   PREC_MIXED, DcsdError, dcsd_heff)
+from ._lib import (CCSD, DCSD, MEM_DEVICE, MEM_HOST, PREC_BF16, PREC_BF16X3, PREC_BF16X6,  # noqa: F401
+                   PREC_FP64, PREC_MIXED, DcsdError, dcsd_heff)
 
-__all__ = ["Engine", "CCSD", "DCSD", "PREC_FP64", "PREC_BF16", "PREC_BF16X3", "PREC_MIXED",
+__all__ = ["Engine", "CCSD", "DCSD", "PREC_FP64", "PREC_BF16", "PREC_BF16X3", "PREC_BF16X6", "PREC_MIXED",
            "dcsd_heff", "DcsdError"]
 
 

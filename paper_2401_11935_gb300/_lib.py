@@ -18,10 +18,11 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5:
           6: "NUMERIC", 7: "NO_DEVICE"}
 CCSD, DCSD = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
-PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED = 0, 1, 2, 3
+PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
-           "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches"]
+           "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile"]
+PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
 class dcsd_dims(C.Structure):
@@ -69,6 +70,8 @@ def load():
     lib.dcsd_last_error.restype = C.c_char_p
     lib.dcsd_kernel_launches.argtypes = [P]
     lib.dcsd_kernel_launches.restype = C.c_longlong
+    lib.dcsd_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    lib.dcsd_profile.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -131,3 +134,14 @@ def dcsd_destroy(ctx):
 
 def dcsd_kernel_launches(ctx):
     return load().dcsd_kernel_launches(ctx)
+
+
+def dcsd_profile(ctx, enable, reset, read=True):
+    """Returns {class: (ms, launches)} when read is True."""
+    lib = load()
+    ms = (C.c_double * 8)()
+    ln = (C.c_longlong * 8)()
+    _check(lib.dcsd_profile(ctx, enable, reset, ms if read else None, ln if read else None), ctx)
+    if not read:
+        return None
+    return {PROF_CLASSES[k]: (ms[k], ln[k]) for k in range(8)}

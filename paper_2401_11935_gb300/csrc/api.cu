@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 using namespace dcsd;
@@ -130,9 +132,9 @@ dcsd_status alloc(Ctx* c, double** p, size_t n) {
 
 void free_ctx(Ctx* c) {
     double** ptrs[] = {&c->B, &c->fock[0], &c->fock[1], &c->Kref[0][0], &c->Kref[0][1],
-                       &c->Kref[1][0], &c->Kref[1][1], &c->t1, &c->R1, &c->Bd, &c->Pbt, &c->fd,
+                       &c->Kref[1][0], &c->Kref[1][1], &c->t1, &c->R1, &c->t2s, &c->Bd, &c->Pbt, &c->fd,
                        &c->fsc, &c->Z, &c->J, &c->H, &c->G, &c->Wo, &c->Foc, &c->Fvi, &c->big0,
-                       &c->big1, &c->big2, &c->big3, &c->red, &c->scal, &c->c1, &c->diis_t,
+                       &c->big1, &c->big2, &c->big3, &c->red, &c->splitk_ws, &c->scal, &c->c1, &c->diis_t,
                        &c->diis_e, &c->abi[0], &c->abi[1], &c->abi[2], &c->abi[3], &c->abi[4],
                        &c->abi[5], &c->abi[6], &c->abi[7], &c->abi[8], &c->abi[9]};
     for (auto pp : ptrs) {
@@ -143,6 +145,13 @@ void free_ctx(Ctx* c) {
     c->R2 = nullptr;
     if (c->hostbuf) cudaFreeHost(c->hostbuf);
     c->hostbuf = nullptr;
+    for (int k = 0; k < 8; ++k) {
+        for (auto& e : c->prof_ev[k]) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        c->prof_ev[k].clear();
+    }
     mtables_free(c);
     tc_free(c);
 }
@@ -161,7 +170,20 @@ dcsd_status sync_scalars(Ctx* c, int count) {
     return DCSD_OK;
 }
 
-bool valid_prec(int p) { return p == DCSD_PREC_FP64 || p == DCSD_PREC_BF16 || p == DCSD_PREC_BF16X3; }
+// the tensor-core kernels record a bounded-wait expiry in scal[22] (int)
+bool tc_timeout(Ctx* c) {
+    int flag;
+    std::memcpy(&flag, &c->hostbuf[22], sizeof(int));
+    if (flag != 0) {
+        c->err = "tensor-core pipeline wait expired (code " + std::to_string(flag) + ")";
+        return true;
+    }
+    return false;
+}
+
+bool valid_prec(int p) {
+    return p == DCSD_PREC_FP64 || p == DCSD_PREC_BF16 || p == DCSD_PREC_BF16X3 || p == DCSD_PREC_BF16X6;
+}
 
 }  // namespace
 
@@ -202,6 +224,12 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
     c->device = dev;
     c->num_sms = prop.multiProcessorCount;
     c->stream = (cudaStream_t)stream;
+    {
+        const char* tr = getenv("DCSD_TRACE");
+        c->trace = tr && tr[0] == '1';
+        const char* vb = getenv("DCSD_VERBOSE");
+        c->verbose = vb && vb[0] == '1';
+    }
     c->nc = d->n_c;
     c->nv = d->n_v;
     c->X = d->naux;
@@ -231,6 +259,7 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
     A_(c->R1, n1 + n2);
     c->R2 = c->R1 + n1;
     A_(c->c1, n1);
+    A_(c->t2s, n2);
     A_(c->Bd, 2 * X * n * n);
     A_(c->Pbt, X * n * O);
     A_(c->fd, 2 * n * n);
@@ -247,6 +276,8 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
     A_(c->big2, c->big_elems);
     A_(c->big3, c->big_elems);
     A_(c->red, 1024);
+    c->splitk_elems = std::max<size_t>(1 << 20, std::min<size_t>(64ul << 20, 16 * (n * n + O * V)));
+    A_(c->splitk_ws, c->splitk_elems);
     A_(c->scal, 64);
 #undef A_
     if (cudaMallocHost((void**)&c->hostbuf, 64 * sizeof(double)) != cudaSuccess) {
@@ -275,6 +306,7 @@ extern "C" dcsd_status dcsd_destroy(dcsd_ctx* h) {
     if (!h) return DCSD_OK;
     Ctx* c = &h->c;
     cudaStreamSynchronize(c->stream);
+    trace_report(c);
     free_ctx(c);
     delete h;
     return DCSD_OK;
@@ -286,6 +318,28 @@ extern "C" const char* dcsd_last_error(const dcsd_ctx* h) {
 }
 
 extern "C" long long dcsd_kernel_launches(const dcsd_ctx* h) { return h ? h->c.launches : 0; }
+
+extern "C" dcsd_status dcsd_profile(dcsd_ctx* h, int enable, int reset, double* ms, long long* launches) {
+    if (!h) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    if (ms || launches) {
+        DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < DCSD_PROF_NCLASS; ++k) {
+            double sum = 0.0;
+            for (size_t i = 0; i < c->prof_used[k]; ++i) {
+                float t = 0.f;
+                DCSD_CUDA(c, cudaEventElapsedTime(&t, c->prof_ev[k][i].first, c->prof_ev[k][i].second));
+                sum += t;
+            }
+            if (ms) ms[k] = sum;
+            if (launches) launches[k] = (long long)c->prof_used[k];
+        }
+    }
+    if (reset)
+        for (int k = 0; k < DCSD_PROF_NCLASS; ++k) c->prof_used[k] = 0;
+    c->prof_on = enable != 0;
+    return DCSD_OK;
+}
 
 static dcsd_status residual_common(Ctx* c, int ref, int method, int prec, int mem_kind,
                                    const double* const* T, double* const* R, double* W, double* dEA) {
@@ -332,7 +386,8 @@ static dcsd_status residual_common(Ctx* c, int ref, int method, int prec, int me
             DCSD_CUDA(c, cudaMemcpyAsync(R[k], Rd[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
                                          c->stream));
     }
-    DCSD_TRY(sync_scalars(c, 21));
+    DCSD_TRY(sync_scalars(c, 23));
+    if (tc_timeout(c)) return DCSD_ERR_TIMEOUT;
     if (W) *W = c->hostbuf[0];
     if (dEA) *dEA = c->hostbuf[1];
     if (c->hostbuf[20] != 0.0 || !std::isfinite(c->hostbuf[0]) || !std::isfinite(c->hostbuf[1])) {
@@ -448,13 +503,12 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
         c->diis_cap = nd;
     }
-    double* step = c->big0;  // scratch vectors (len <= ...) allocated separately below
-    double* tnew = nullptr;
     std::vector<double> Bm(16 * 16, 0.0);
-    std::vector<int> slot_age;
     int nhist = 0, next = 0;
     bool switched = false;
     int switched_at = -1;
+    double best_r = 1e300, best_r_window = 1e300;
+    int stall = 0;
     const double* fa = c->fock[ref == 0 ? 0 : 1];
     const double* fb = c->fock[ref == 0 ? 1 : 0];
     double *sbuf = nullptr, *tbuf = nullptr;
@@ -468,14 +522,17 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     int it = 0;
     for (it = 1; it <= o->maxiter; ++it) {
         int prec = o->precision;
-        if (prec == DCSD_PREC_MIXED) prec = switched ? DCSD_PREC_BF16X3 : DCSD_PREC_BF16;
+        if (prec == DCSD_PREC_MIXED) prec = switched ? DCSD_PREC_BF16X6 : DCSD_PREC_BF16;
         dcsd_status s = residual_union(c, ref, o->method, prec);
         if (s != DCSD_OK) { status = s; break; }
         if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
         DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
         if ((s = check_finite(c, c->R1, len, c->scal + 20)) != DCSD_OK) { status = s; break; }
-        if ((s = sync_scalars(c, 22)) != DCSD_OK) { status = s; break; }
+        if ((s = sync_scalars(c, 23)) != DCSD_OK) { status = s; break; }
+        if (tc_timeout(c)) { status = DCSD_ERR_TIMEOUT; break; }
         const double W = c->hostbuf[0], dE = c->hostbuf[1], rmax = c->hostbuf[21];
+        if (c->verbose)
+            fprintf(stderr, "[dcsd solve] it %3d prec %d max|R| %.3e dEA %.12f W %.12f\n", it, prec, rmax, dE, W);
         res->W = W;
         res->dEA = dE;
         res->max_r = rmax;
@@ -489,13 +546,19 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
             res->converged = 1;
             break;
         }
-        if (o->precision == DCSD_PREC_MIXED && !switched && rmax < o->switch_tol) {
-            switched = true;
-            switched_at = it;
-            nhist = 0;  // history built with the lower precision is discarded
-            next = 0;
+        // MIXED: leave BF16 once max|R| is below switch_tol or has stopped
+        // decreasing (BF16 rounding puts a floor under the residual)
+        if (o->precision == DCSD_PREC_MIXED && !switched) {
+            best_r = std::min(best_r, rmax);
+            if (rmax < best_r_window * 0.5) { best_r_window = rmax; stall = 0; }
+            else ++stall;
+            if (rmax < o->switch_tol || stall >= 6) {
+                switched = true;
+                switched_at = it;
+                nhist = 0;  // history built with the lower precision is discarded
+                next = 0;
+            }
         }
-        if (it == o->maxiter) break;
         double* st_v = nd > 0 ? c->diis_e + (size_t)next * len : sbuf;
         double* tn_v = nd > 0 ? c->diis_t + (size_t)next * len : tbuf;
         k_jacobi<<<grid_n(c, len), 256, 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, c->t1, c->R1,
@@ -554,9 +617,6 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         k_lincomb<<<grid_n(c, len), 256, 0, c->stream>>>(lc, len, c->t1);
         if ((s = launch_check(c, "diis_extrapolate")) != DCSD_OK) { status = s; break; }
     }
-    (void)step;
-    (void)tnew;
-    (void)slot_age;
     if (sbuf) cudaFree(sbuf);
     if (tbuf) cudaFree(tbuf);
     res->iters = std::min(it, o->maxiter);

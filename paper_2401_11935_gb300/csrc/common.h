@@ -73,6 +73,7 @@ struct Ctx {
     // working tensors (device, FP64), union layout
     double* t1 = nullptr;         // [2][O][V]
     double* t2 = nullptr;         // [3][O][O][V][V] (aa, bb, ab)
+    double* t2s = nullptr;        // t2 with the two virtual indices exchanged (coupling terms)
     double* R1 = nullptr;         // [2][O][V]
     double* R2 = nullptr;         // [3][O][O][V][V]
     double* Bd = nullptr;         // [2][X][n][n] T1-dressed DF factors
@@ -93,6 +94,8 @@ struct Ctx {
     size_t big_elems = 0;
     double* abi[10] = {};         // device staging of ABI arrays for host mem_kind calls
     double* red = nullptr;        // reduction scratch
+    double* splitk_ws = nullptr;  // split-K partial tiles of the FP64 contraction kernel
+    size_t splitk_elems = 0;
     double* scal = nullptr;       // device scalars: [0]=W [1]=dEA [2..] misc
     double* c1 = nullptr;         // [2][O][V] two-determinant coefficients
     double* hostbuf = nullptr;    // pinned host staging for scalars
@@ -100,6 +103,17 @@ struct Ctx {
 
     MTables* mt[2] = {};          // per reference
     TcEngine* tc = nullptr;
+
+    // optional device-time accounting (dcsd_profile)
+    bool prof_on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[8];
+    size_t prof_used[8] = {};
+    int ladder_phase = 0;         // set while the ladder GEMMs run (profile class)
+    // DCSD_TRACE=1: per-call device time by label, summarised to stderr on destroy
+    bool trace = false;
+    bool verbose = false;         // DCSD_VERBOSE=1: per-iteration solver log on stderr
+    std::string cur_spec;
+    std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
 
     // solver state (device)
     double* diis_t = nullptr;     // [nd][len]
@@ -151,6 +165,7 @@ dcsd_status apply_mterms(Ctx* c, int ref);
 
 // residual orchestration (residual.cu)
 dcsd_status residual_union(Ctx* c, int ref, int method, int precision);
+dcsd_status add_fock_hh(Ctx* c, double* Wo, const double* F1, const double* F2);
 dcsd_status init_constants(Ctx* c);
 
 // tensor-core engine (tc_gemm.cu)
@@ -161,8 +176,40 @@ void tc_free(Ctx* c);
 dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A,
                       const TV& B, double beta, const TV& C, int nsplit);
 
-// solver helpers (api.cu / solve kernels)
-dcsd_status jacobi_step(Ctx* c, int ref, double* step_out);
+// pp ladder + its T1 correction on tensor cores (R2 += ladder, G = correction)
+dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G);
+
+// record a CUDA event pair around a launch of class cls when profiling
+inline void prof_begin(Ctx* c, int cls) {
+    if (!c->prof_on) return;
+    auto& v = c->prof_ev[cls];
+    if (c->prof_used[cls] == v.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        v.push_back({a, b});
+    }
+    cudaEventRecord(v[c->prof_used[cls]].first, c->stream);
+}
+inline void prof_end(Ctx* c, int cls) {
+    if (!c->prof_on) return;
+    cudaEventRecord(c->prof_ev[cls][c->prof_used[cls]].second, c->stream);
+    c->prof_used[cls]++;
+}
+
+inline void trace_begin(Ctx* c, const std::string& label) {
+    if (!c->trace) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+    c->trace_ev.push_back({label, {a, b}});
+}
+inline void trace_end(Ctx* c) {
+    if (!c->trace || c->trace_ev.empty()) return;
+    cudaEventRecord(c->trace_ev.back().second.second, c->stream);
+}
+void trace_report(Ctx* c);
 
 inline dcsd_status launch_check(Ctx* c, const char* what) {
     cudaError_t e = cudaGetLastError();

@@ -10,6 +10,7 @@
 #include "common.h"
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 namespace dcsd {
@@ -216,6 +217,8 @@ bool plan_einsum(const char* spec, const TV& A, const TV& B, const TV& C,
     return true;
 }
 
+static unsigned grid_for(Ctx* c, long total);
+
 // ---------------------------------------------------------------------------
 // FP64 tiled GEMM over a GemmPlan
 // ---------------------------------------------------------------------------
@@ -226,6 +229,9 @@ struct GemmArgs {
     double alpha, beta;
     GemmPlan p;
     int a_kfast, b_kfast;
+    int nsplit;        // > 1: blockIdx.z = K split, partial tiles -> ws[split][m][n]
+    long kchunk;
+    double* ws;
 };
 
 __device__ __forceinline__ void decomp2(long idx, int nmode, const long* size, const long* s1,
@@ -254,7 +260,10 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
     const GemmPlan& p = g.p;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long m0 = (long)blockIdx.x * GBM, n0 = (long)blockIdx.y * GBN;
-    for (long bz = blockIdx.z; bz < p.NB; bz += gridDim.z) {
+    const long nbz = g.nsplit > 1 ? 1 : p.NB;
+    const long kb = g.nsplit > 1 ? blockIdx.z * g.kchunk : 0;
+    const long ke = g.nsplit > 1 ? min(p.K, kb + g.kchunk) : p.K;
+    for (long bz = g.nsplit > 1 ? 0 : blockIdx.z; bz < nbz; bz += gridDim.z) {
         long oA = 0, oB = 0, oC = 0;
         {
             long idx = bz;
@@ -280,11 +289,11 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-        for (long k0 = 0; k0 < p.K; k0 += GBK) {
+        for (long k0 = kb; k0 < ke; k0 += GBK) {
             __syncthreads();
             if (tid < GBK) {
                 long k = k0 + tid;
-                if (k < p.K) decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, kA[tid], kB[tid]);
+                if (k < ke) decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, kA[tid], kB[tid]);
                 else { kA[tid] = -1; kB[tid] = -1; }
             }
             __syncthreads();
@@ -316,6 +325,19 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
                     for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
             }
         }
+        if (g.nsplit > 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const long m = m0 + ty + 16 * i;
+                if (m >= p.M) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long nn = n0 + tx + 16 * j;
+                    if (nn < p.N) g.ws[((long)blockIdx.z * p.M + m) * p.N + nn] = acc[i][j];
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             long rc = rC[ty + 16 * i];
@@ -329,6 +351,53 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
                 if (g.beta != 0.0) v += g.beta * (*cp);
                 *cp = v;
             }
+        }
+    }
+}
+
+// ordered reduction of split-K partials: C = alpha * sum_s ws[s] + beta * C
+__global__ void k_splitk_reduce(GemmPlan p, int nsplit, const double* ws, double* C, double alpha,
+                                double beta) {
+    const long total = p.M * p.N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        const long m = e / p.N, n = e - m * p.N;
+        double s = 0.0;
+        for (int k = 0; k < nsplit; ++k) s += ws[(long)k * total + e];
+        long ra, rc, cb, cc;
+        decomp2(m, p.nm, p.m_size, p.m_sa, p.m_sc, ra, rc);
+        decomp2(n, p.nn, p.n_size, p.n_sb, p.n_sc, cb, cc);
+        double* cp = C + rc + cc;
+        double v = alpha * s;
+        if (beta != 0.0) v += beta * (*cp);
+        *cp = v;
+    }
+}
+
+// matrix-vector shaped contractions (one output side of extent 1): one warp
+// per output element, lanes stride over k
+__global__ void __launch_bounds__(256) k_gemv64(GemmArgs g, int vec_is_b) {
+    const GemmPlan& p = g.p;
+    const long P = vec_is_b ? p.M : p.N;
+    const int lane = threadIdx.x & 31;
+    for (long o = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; o < P;
+         o += ((long)gridDim.x * blockDim.x) >> 5) {
+        long oa, oc, ob = 0;
+        if (vec_is_b) decomp2(o, p.nm, p.m_size, p.m_sa, p.m_sc, oa, oc);
+        else { decomp2(o, p.nn, p.n_size, p.n_sb, p.n_sc, ob, oc); oa = 0; }
+        double s = 0.0;
+        for (long k = lane; k < p.K; k += 32) {
+            long ka, kb;
+            decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, ka, kb);
+            s = fma(g.A[oa + ka], g.B[ob + kb], s);
+        }
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+        if (lane == 0) {
+            double* cp = g.C + oc;
+            double v = g.alpha * s;
+            if (g.beta != 0.0) v += g.beta * (*cp);
+            *cp = v;
         }
     }
 }
@@ -349,9 +418,48 @@ dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A, const 
     g.beta = beta;
     g.a_kfast = (g.p.nk > 0 && g.p.k_sa[g.p.nk - 1] == 1) ? 1 : 0;
     g.b_kfast = (g.p.nk > 0 && g.p.k_sb[g.p.nk - 1] == 1) ? 1 : 0;
+    g.nsplit = 1;
+    g.kchunk = g.p.K;
+    g.ws = nullptr;
+    if (g.p.NB == 1 && (g.p.N == 1 || g.p.M == 1) && g.p.K >= 64) {
+        const int vec_is_b = g.p.N == 1 ? 1 : 0;
+        const long outs = vec_is_b ? g.p.M : g.p.N;
+        prof_begin(c, DCSD_PROF_FP64);
+        if (c->trace)
+            trace_begin(c, std::string("fp64-gemv ") + spec + " M=" + std::to_string(g.p.M) + " N=" +
+                               std::to_string(g.p.N) + " K=" + std::to_string(g.p.K));
+        k_gemv64<<<grid_for(c, outs * 32), 256, 0, c->stream>>>(g, vec_is_b);
+        trace_end(c);
+        prof_end(c, DCSD_PROF_FP64);
+        return launch_check(c, spec);
+    }
+    const long tiles = ((g.p.M + GBM - 1) / GBM) * ((g.p.N + GBN - 1) / GBN);
+    if (g.p.NB == 1 && tiles < c->num_sms && g.p.K >= 2048 && c->splitk_ws) {
+        // few output tiles and a long contraction: split K over CTAs
+        long ns = std::min<long>((2 * c->num_sms + tiles - 1) / tiles, g.p.K / 512);
+        ns = std::min<long>(ns, (long)(c->splitk_elems / std::max<long>(1, g.p.M * g.p.N)));
+        ns = std::min<long>(ns, 65535);
+        if (ns >= 2) {
+            g.nsplit = (int)ns;
+            g.kchunk = ((g.p.K + ns - 1) / ns + GBK - 1) / GBK * GBK;
+            g.nsplit = (int)((g.p.K + g.kchunk - 1) / g.kchunk);
+            g.ws = c->splitk_ws;
+        }
+    }
     dim3 grid((unsigned)((g.p.M + GBM - 1) / GBM), (unsigned)((g.p.N + GBN - 1) / GBN),
-              (unsigned)std::min<long>(g.p.NB, 65535));
+              (unsigned)(g.nsplit > 1 ? g.nsplit : std::min<long>(g.p.NB, 65535)));
+    prof_begin(c, DCSD_PROF_FP64);
+    if (c->trace)
+        trace_begin(c, std::string("fp64 ") + spec + " M=" + std::to_string(g.p.M) + " N=" +
+                           std::to_string(g.p.N) + " K=" + std::to_string(g.p.K) + " B=" +
+                           std::to_string(g.p.NB) + " split=" + std::to_string(g.nsplit));
     k_gemm64<<<grid, 256, 0, c->stream>>>(g);
+    if (g.nsplit > 1) {
+        long tot = g.p.M * g.p.N;
+        k_splitk_reduce<<<grid_for(c, tot), 256, 0, c->stream>>>(g.p, g.nsplit, g.ws, g.C, alpha, beta);
+    }
+    trace_end(c);
+    prof_end(c, DCSD_PROF_FP64);
     return launch_check(c, spec);
 }
 
@@ -604,4 +712,30 @@ dcsd_status check_finite(Ctx* c, const double* p, size_t n, double* flag) {
     return launch_check(c, "check_finite");
 }
 
+}  // namespace dcsd
+
+namespace dcsd {
+void trace_report(Ctx* c) {
+    if (!c->trace || c->trace_ev.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    struct Agg { double ms = 0; long n = 0; };
+    std::vector<std::pair<std::string, Agg>> agg;
+    double total = 0;
+    for (auto& e : c->trace_ev) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e.second.first, e.second.second);
+        total += t;
+        auto it = std::find_if(agg.begin(), agg.end(), [&](auto& x) { return x.first == e.first; });
+        if (it == agg.end()) { agg.push_back({e.first, Agg()}); it = agg.end() - 1; }
+        it->second.ms += t;
+        it->second.n++;
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    c->trace_ev.clear();
+    std::sort(agg.begin(), agg.end(), [](auto& a, auto& b) { return a.second.ms > b.second.ms; });
+    fprintf(stderr, "[dcsd trace] total traced %.3f ms\n", total);
+    for (auto& a : agg)
+        fprintf(stderr, "[dcsd trace] %10.3f ms %5ld x  %s\n", a.second.ms, a.second.n, a.first.c_str());
+}
 }  // namespace dcsd

@@ -29,25 +29,35 @@
 
 namespace dcsd {
 
+// One amplitude factor of a coupling term.  arr: 0 T1a, 1 T1b, 2 T2aa,
+// 3 T2bb, 4 T2ab, 5..7 the T2 blocks with the two virtual indices exchanged
+// (so that the element's b index is always the contiguous one).  Index codes:
+// 0..3 the element's i, j, a, b; 4/5 the open orbitals t/u as occupied
+// (union occ positions n_c, n_c+1); 6/7 t/u as virtual (union vir 0, 1).
 struct MFac {
-    int arr;      // 0 T1a, 1 T1b, 2 T2aa, 3 T2bb, 4 T2ab (this frame, union layout)
-    int idx[4];   // >= 0: union position; -1..-4: the element's i, j, a, b
+    int8_t arr;
+    int8_t idx[4];
 };
 struct MTerm {
-    double coef;
-    int nf;
+    int8_t sign;
+    int8_t nf;
     MFac f[4];
 };
 constexpr int kNumClasses = 56;  // 48 doubles classes + 8 singles classes
+constexpr int kMaxTerms = 640;
 
 struct MTables {
     std::vector<MTerm> terms;
     int off[kNumClasses];
     int cnt[kNumClasses];
-    MTerm* d_terms = nullptr;
-    int* d_off = nullptr;
-    int* d_cnt = nullptr;
 };
+
+// tables of both references, identical for every context (they depend only
+// on which of q's indices are open orbitals, not on the sizes)
+__constant__ MTerm c_terms[2][kMaxTerms];
+__constant__ int c_off[2][kNumClasses];
+__constant__ int c_cnt[2][kNumClasses];
+static bool g_tables_ready[64] = {};
 
 namespace {
 
@@ -142,7 +152,9 @@ void expand(const std::vector<Tok>& I, const std::vector<Tok>& A, std::vector<ST
 }  // namespace
 
 static dcsd_status derive_tables(Ctx* c, int ref, MTables& mt) {
-    const int n = c->n, nc = c->nc, nv = c->nv;
+    // representative sizes: enough core and external orbitals for two
+    // distinct free indices of one kind plus a second set to check signs
+    const int nc = 4, nv = 4, n = nc + 2 + nv;
     const int t = nc, u = nc + 1;
     // spatial active orbitals of this frame: occ[spin], vir[spin]
     const int occ_sp[2] = {ref == 0 ? t : u, ref == 0 ? u : t};
@@ -229,43 +241,49 @@ static dcsd_status derive_tables(Ctx* c, int ref, MTables& mt) {
         std::vector<STerm> st;
         expand(It, At, st);
         auto spin_of = [&](const Tok& x) { return x.gid / n; };
-        auto pos = [&](const Tok& x, bool occ) {
-            if (x.slot >= 0) return -1 - x.slot;
-            int sp = x.gid % n;
-            return occ ? sp : sp - nc;
+        // slot codes: 0..3 the element's own index; 4/5 occupied t/u; 6/7 virtual t/u
+        auto code = [&](const Tok& x, bool occ) -> int {
+            if (x.slot >= 0) return x.slot;
+            const int sp = x.gid % n;
+            return (occ ? 4 : 6) + (sp == t ? 0 : 1);
         };
         mt.off[cls] = (int)mt.terms.size();
         for (auto& term : st) {
             MTerm m;
-            m.coef = (double)(s * term.sign);
-            m.nf = (int)term.f.size();
+            int sign = s * term.sign;
+            m.nf = (int8_t)term.f.size();
             bool ok = true;
             for (int k = 0; k < m.nf; ++k) {
                 const SFac& f = term.f[k];
                 MFac& g = m.f[k];
                 if (f.kind == 1) {
                     if (spin_of(f.t[0]) != spin_of(f.t[1])) { ok = false; break; }
-                    g.arr = 1 - spin_of(f.t[0]);  // flip: T_other(sigma) = T_this(1-sigma)
-                    g.idx[0] = pos(f.t[0], true);
-                    g.idx[1] = pos(f.t[1], false);
-                    g.idx[2] = g.idx[3] = 0;
+                    g.arr = (int8_t)(1 - spin_of(f.t[0]));  // flip: T_other(sigma) = T_this(1-sigma)
+                    g.idx[0] = (int8_t)code(f.t[0], true);
+                    g.idx[1] = (int8_t)code(f.t[1], false);
+                    g.idx[2] = g.idx[3] = 6;
                 } else {
                     int so[2] = {1 - spin_of(f.t[0]), 1 - spin_of(f.t[1])};
                     int sv[2] = {1 - spin_of(f.t[2]), 1 - spin_of(f.t[3])};
                     int no_b = so[0] + so[1], nv_b = sv[0] + sv[1];
                     if (no_b != nv_b) { ok = false; break; }
-                    int o0 = pos(f.t[0], true), o1 = pos(f.t[1], true);
-                    int v0 = pos(f.t[2], false), v1 = pos(f.t[3], false);
-                    if (no_b == 0) { g.arr = 2; }
-                    else if (no_b == 2) { g.arr = 3; }
+                    int o0 = code(f.t[0], true), o1 = code(f.t[1], true);
+                    int v0 = code(f.t[2], false), v1 = code(f.t[3], false);
+                    int arr;
+                    if (no_b == 0) { arr = 2; }
+                    else if (no_b == 2) { arr = 3; }
                     else {
-                        g.arr = 4;
-                        if (so[0] == 1) { std::swap(o0, o1); m.coef = -m.coef; }
-                        if (sv[0] == 1) { std::swap(v0, v1); m.coef = -m.coef; }
+                        arr = 4;
+                        if (so[0] == 1) { std::swap(o0, o1); sign = -sign; }
+                        if (sv[0] == 1) { std::swap(v0, v1); sign = -sign; }
                     }
-                    g.idx[0] = o0; g.idx[1] = o1; g.idx[2] = v0; g.idx[3] = v1;
+                    // keep the element's b (code 3) in the contiguous slot
+                    if (v0 == 3) { std::swap(v0, v1); arr += 3; }
+                    g.arr = (int8_t)arr;
+                    g.idx[0] = (int8_t)o0; g.idx[1] = (int8_t)o1; g.idx[2] = (int8_t)v0; g.idx[3] = (int8_t)v1;
                 }
             }
+            m.sign = (int8_t)sign;
             if (ok) mt.terms.push_back(m);
         }
         mt.cnt[cls] = (int)mt.terms.size() - mt.off[cls];
@@ -292,67 +310,65 @@ static dcsd_status derive_tables(Ctx* c, int ref, MTables& mt) {
 }
 
 dcsd_status mtables_build(Ctx* c) {
+    if (c->device >= 0 && c->device < 64 && g_tables_ready[c->device]) return DCSD_OK;
+    static MTerm h_terms[2][kMaxTerms];
+    static int h_off[2][kNumClasses], h_cnt[2][kNumClasses];
     for (int ref = 0; ref < 2; ++ref) {
-        MTables* mt = new MTables();
-        c->mt[ref] = mt;
-        DCSD_TRY(derive_tables(c, ref, *mt));
-        size_t nb = std::max<size_t>(1, mt->terms.size()) * sizeof(MTerm);
-        DCSD_CUDA(c, cudaMalloc(&mt->d_terms, nb));
-        DCSD_CUDA(c, cudaMalloc(&mt->d_off, sizeof(mt->off)));
-        DCSD_CUDA(c, cudaMalloc(&mt->d_cnt, sizeof(mt->cnt)));
-        if (!mt->terms.empty())
-            DCSD_CUDA(c, cudaMemcpy(mt->d_terms, mt->terms.data(), mt->terms.size() * sizeof(MTerm),
-                                    cudaMemcpyHostToDevice));
-        DCSD_CUDA(c, cudaMemcpy(mt->d_off, mt->off, sizeof(mt->off), cudaMemcpyHostToDevice));
-        DCSD_CUDA(c, cudaMemcpy(mt->d_cnt, mt->cnt, sizeof(mt->cnt), cudaMemcpyHostToDevice));
+        MTables mt;
+        DCSD_TRY(derive_tables(c, ref, mt));
+        if (mt.terms.size() > (size_t)kMaxTerms) {
+            c->err = "two-determinant table larger than its constant-memory slot";
+            return DCSD_ERR_INVALID_ARG;
+        }
+        std::memset(h_terms[ref], 0, sizeof(h_terms[ref]));
+        std::copy(mt.terms.begin(), mt.terms.end(), h_terms[ref]);
+        std::memcpy(h_off[ref], mt.off, sizeof(mt.off));
+        std::memcpy(h_cnt[ref], mt.cnt, sizeof(mt.cnt));
     }
+    DCSD_CUDA(c, cudaMemcpyToSymbol(c_terms, h_terms, sizeof(h_terms)));
+    DCSD_CUDA(c, cudaMemcpyToSymbol(c_off, h_off, sizeof(h_off)));
+    DCSD_CUDA(c, cudaMemcpyToSymbol(c_cnt, h_cnt, sizeof(h_cnt)));
+    if (c->device >= 0 && c->device < 64) g_tables_ready[c->device] = true;
     return DCSD_OK;
 }
 
-void mtables_free(Ctx* c) {
-    for (int ref = 0; ref < 2; ++ref) {
-        MTables* mt = c->mt[ref];
-        if (!mt) continue;
-        cudaFree(mt->d_terms);
-        cudaFree(mt->d_off);
-        cudaFree(mt->d_cnt);
-        delete mt;
-        c->mt[ref] = nullptr;
-    }
-}
+void mtables_free(Ctx* c) { (void)c; }
 
 // ---------------------------------------------------------------------------
 // device evaluation
 // ---------------------------------------------------------------------------
 struct MArgs {
-    int O, V, nc;
+    int O, V, nc, ref;
     int occ_act[2], vir_act[2];
     const double* t1;  // [2][O][V]
     const double* t2;  // [3][O][O][V][V]
+    const double* t2s; // [3][O][O][V][V] with the virtual indices exchanged
     double* R1;
     double* R2;
     double* c1;        // [2][O][V]
     const double* W;   // device scalar
-    const MTerm* terms;
-    const int* off;
-    const int* cnt;
 };
 
 __device__ __forceinline__ double eval_class(const MArgs& a, int cls, const int q[4]) {
-    const long O = a.O, V = a.V;
+    const long O = a.O, V = a.V, nb = O * O * V * V;
+    // code -> union position
+    const int pos[8] = {q[0], q[1], q[2], q[3], a.nc, a.nc + 1, 0, 1};
     double sum = 0.0;
-    const int o = a.off[cls], n = a.cnt[cls];
+    const int o = c_off[a.ref][cls], n = c_cnt[a.ref][cls];
     for (int k = 0; k < n; ++k) {
-        const MTerm& m = a.terms[o + k];
-        double prod = m.coef;
+        const MTerm& m = c_terms[a.ref][o + k];
+        double prod = (double)m.sign;
         for (int f = 0; f < m.nf; ++f) {
             const MFac& g = m.f[f];
-            int x[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) x[r] = g.idx[r] >= 0 ? g.idx[r] : q[-1 - g.idx[r]];
+            const int x0 = pos[g.idx[0]], x1 = pos[g.idx[1]];
             double val;
-            if (g.arr < 2) val = a.t1[((long)g.arr * O + x[0]) * V + x[1]];
-            else val = a.t2[((((long)(g.arr - 2) * O + x[0]) * O + x[1]) * V + x[2]) * V + x[3]];
+            if (g.arr < 2) {
+                val = a.t1[((long)g.arr * O + x0) * V + x1];
+            } else {
+                const int x2 = pos[g.idx[2]], x3 = pos[g.idx[3]];
+                const double* base = g.arr < 5 ? a.t2 + (g.arr - 2) * nb : a.t2s + (g.arr - 5) * nb;
+                val = base[(((long)x0 * O + x1) * V + x2) * V + x3];
+            }
             prod *= val;
         }
         sum += prod;
@@ -435,15 +451,41 @@ __global__ void k_mterm_doubles(MArgs a) {
     }
 }
 
+// t2s[blk][i][j][b][a] = t2[blk][i][j][a][b] (32x32 tiles through shared memory)
+__global__ void k_swap_vir(long nmat, int V, const double* t2, double* t2s) {
+    __shared__ double tile[32][33];
+    const long tv = (V + 31) / 32;
+    for (long t = blockIdx.x; t < nmat * tv * tv; t += gridDim.x) {
+        const long mat = t / (tv * tv);
+        const int ta = (int)((t / tv) % tv), tb = (int)(t % tv);
+        const double* src = t2 + mat * (long)V * V;
+        double* dst = t2s + mat * (long)V * V;
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int aa = ta * 32 + e / 32, bb = tb * 32 + e % 32;
+            tile[e / 32][e % 32] = (aa < V && bb < V) ? src[(long)aa * V + bb] : 0.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int bb = tb * 32 + e / 32, aa = ta * 32 + e % 32;
+            if (aa < V && bb < V) dst[(long)bb * V + aa] = tile[e % 32][e / 32];
+        }
+        __syncthreads();
+    }
+}
+
 dcsd_status apply_mterms(Ctx* c, int ref) {
-    MTables* mt = c->mt[ref];
     MArgs a;
-    a.O = c->O; a.V = c->V; a.nc = c->nc;
+    a.O = c->O; a.V = c->V; a.nc = c->nc; a.ref = ref;
     Frame f = frame_of(c, ref);
     for (int s = 0; s < 2; ++s) { a.occ_act[s] = f.occ_act[s]; a.vir_act[s] = f.vir_act[s]; }
-    a.t1 = c->t1; a.t2 = c->t2; a.R1 = c->R1; a.R2 = c->R2; a.c1 = c->c1;
+    a.t1 = c->t1; a.t2 = c->t2; a.t2s = c->t2s; a.R1 = c->R1; a.R2 = c->R2; a.c1 = c->c1;
     a.W = c->scal;
-    a.terms = mt->d_terms; a.off = mt->d_off; a.cnt = mt->d_cnt;
+    {
+        const long nmat = 3l * c->O * c->O, tv = (c->V + 31) / 32;
+        const long blocks = std::min<long>(nmat * tv * tv, (long)std::max(c->num_sms, 1) * 16);
+        k_swap_vir<<<(unsigned)std::max<long>(1, blocks), 256, 0, c->stream>>>(nmat, c->V, c->t2, c->t2s);
+        DCSD_TRY(launch_check(c, "swap_vir"));
+    }
     long n1 = 2l * c->O * c->V;
     k_mterm_singles<<<(unsigned)std::max<long>(1, (n1 + 255) / 256), 256, 0, c->stream>>>(a);
     DCSD_TRY(launch_check(c, "mterm_singles"));

@@ -53,6 +53,26 @@ dcsd_status init_constants(Ctx* c) {
     return DCSD_OK;
 }
 
+__global__ void k_add_fock_hh(int O, double* Wo, const double* F1, const double* F2) {
+    const long total = (long)O * O * O * O;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % O), i = (int)((e / O) % O), l = (int)((e / O / O) % O),
+                  k = (int)(e / O / O / O);
+        double d = 0.0;
+        if (k == i) d += F2[l * O + j];
+        if (l == j) d += F1[k * O + i];
+        Wo[e] -= d;
+    }
+}
+
+dcsd_status add_fock_hh(Ctx* c, double* Wo, const double* F1, const double* F2) {
+    const long total = (long)c->O * c->O * c->O * c->O;
+    k_add_fock_hh<<<(unsigned)std::max<long>(1, std::min<long>((total + 255) / 256, 4096)), 256, 0,
+                    c->stream>>>(c->O, Wo, F1, F2);
+    return launch_check(c, "add_fock_hh");
+}
+
 __global__ void k_energy_combine(double* s) {
     // s[1] = f.t1 ; s[2..4] = J.t2 (aa, bb, ab); s[5..6] direct/exchange t1 t1 (aa);
     // s[7..8] (bb); s[9] ab direct
@@ -64,14 +84,25 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     const double x = method == DCSD_CCSD ? 1.0 : 0.0;
     const double y = method == DCSD_CCSD ? 1.0 : 0.5;
     const Frame fr = frame_of(c, ref);
-    const int nsplit = prec == DCSD_PREC_BF16X3 ? 2 : 1;
+    const int nsplit = prec == DCSD_PREC_BF16X6 ? 3 : prec == DCSD_PREC_BF16X3 ? 2 : 1;
     auto big = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
                    const TV& C) -> dcsd_status {
         if (prec == DCSD_PREC_FP64) return einsum64(c, spec, alpha, A, Bm, beta, C);
         return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
     };
+    // small contractions stay FP64; in the tensor-core modes large unbatched
+    // ones (>= 4 GFLOP) go to the tensor cores like the named big ones
     auto sml = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
-                   const TV& C) -> dcsd_status { return einsum64(c, spec, alpha, A, Bm, beta, C); };
+                   const TV& C) -> dcsd_status {
+        if (prec != DCSD_PREC_FP64) {
+            GemmPlan p;
+            std::string e;
+            if (plan_einsum(spec, A, Bm, C, p, e) && p.NB == 1 && p.K >= 16 &&
+                2.0 * (double)p.M * (double)p.N * (double)p.K >= 4e9)
+                return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
+        }
+        return einsum64(c, spec, alpha, A, Bm, beta, C);
+    };
 
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
@@ -160,12 +191,14 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         int s1 = s1_of[b], s2 = s2_of[b];
         DCSD_TRY(big("bc,ijac->ijab", 1.0, blk(Fvi, s2), blk(t2, b), 1.0, blk(R2, b)));
         DCSD_TRY(big("ac,ijcb->ijab", 1.0, blk(Fvi, s1), blk(t2, b), 1.0, blk(R2, b)));
-        DCSD_TRY(big("kj,ikab->ijab", -1.0, blk(Foc, s2), blk(t2, b), 1.0, blk(R2, b)));
-        DCSD_TRY(big("ki,kjab->ijab", -1.0, blk(Foc, s1), blk(t2, b), 1.0, blk(R2, b)));
     }
 
     // ---- particle-particle ladder (undressed (ac|bd), stacked blocks) --------
-    {
+    TV G = view(c->G, {4, O, O, O, V});
+    TV H = view(c->H, {3, O, O, O, O});
+    if (prec != DCSD_PREC_FP64) {
+        DCSD_TRY(ladder_tc(c, nsplit, c->R2, c->G));
+    } else {
         long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
         for (long a0 = 0; a0 < V; a0 += ch) {
             long na = std::min(ch, V - a0);
@@ -173,11 +206,8 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
             DCSD_TRY(big("Lac,Lbd->acbd", 1.0, sub(Bvv, 1, a0, na), Bvv, 0.0, Vc));
             DCSD_TRY(big("sijcd,acbd->sijab", 1.0, t2, Vc, 1.0, sub(R2, 3, a0, na)));
         }
-    }
     // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with t_ab
     // transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
-    TV G = view(c->G, {4, O, O, O, V});
-    TV H = view(c->H, {3, O, O, O, O});
     {
         long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
         for (long k0 = 0; k0 < O; k0 += kc) {
@@ -187,6 +217,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
             DCSD_TRY(big("sijcd,kcbd->sijkb", 1.0, t2, Ic, 0.0, sub(sub(G, 0, 0, 3), 3, k0, nk)));
             DCSD_TRY(big("ijdc,kcbd->ijkb", 1.0, blk(t2, 2), Ic, 0.0, sub(blk(G, 3), 2, k0, nk)));
         }
+    }
     }
     DCSD_TRY(big("kmcd,sijcd->sijkm", 1.0, J, t2, 0.0, H));
     for (int b = 0; b < 3; ++b) {
@@ -206,6 +237,9 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         TV Wo = view(c->Wo, {O, O, O, O});
         DCSD_TRY(sml("Lki,Llj->klij", 1.0, BdOO(s1), BdOO(s2), 0.0, Wo));
         DCSD_TRY(axpy_view(c, cs, perm(blk(H, b), {2, 3, 0, 1}), 1.0, Wo));
+        // occupied Fock terms -P(ij) sum_k F_kj t_ik^ab as part of the same
+        // contraction: Wo[k][l][i][j] -= d_ki F2[l][j] + d_lj F1[k][i]
+        DCSD_TRY(add_fock_hh(c, Wo.p, c->Foc + (long)s1 * O * O, c->Foc + (long)s2 * O * O));
         DCSD_TRY(big("klij,klab->ijab", 1.0, Wo, blk(t2, b), 1.0, blk(R2, b)));
     }
 

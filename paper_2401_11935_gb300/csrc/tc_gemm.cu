@@ -1,11 +1,858 @@
-// placeholder, replaced by the tcgen05 engine
+// Tensor-core contraction engine for sm_103a (tcgen05 + TMEM + TMA).
+//
+// C[m][n] = alpha * sum_k A[m][k] B[n][k] + beta * C with A, B in BF16,
+// K-major, staged in shared memory by TMA (128-byte swizzle) through a
+// 4-stage mbarrier pipeline and multiplied by tcgen05.mma (kind::f16,
+// M = 128, N = 128/256, K = 16 per instruction) into an FP32 accumulator in
+// tensor memory.  Warp roles: warp 0 issues TMA loads, warp 1 owns TMEM and
+// issues the MMAs (one thread), warps 2-5 drain TMEM with tcgen05.ld and
+// write the tile (FP64 C through arbitrary strides, or BF16 directly in the
+// packed operand layout of a following GEMM).
+//
+// Precision: operands are rounded to BF16 (nsplit = 1) or split x = hi + lo
+// with hi, lo BF16 (nsplit = 2) and multiplied as hi*hi + hi*lo + lo*hi by
+// concatenating three segments along K (A: [hi|hi|lo], B: [hi|lo|hi]); the
+// accumulation is FP32 in TMEM, the result is added to the FP64 residual.
+//
+// Every mbarrier wait is bounded (about two seconds of wall time); on
+// expiry the kernel records an error flag, waits (bounded) for its own
+// copies and MMAs in flight, frees its TMEM and returns.
 #include "common.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+
 namespace dcsd {
-dcsd_status tc_init(Ctx* c) { (void)c; return DCSD_OK; }
-void tc_free(Ctx* c) { (void)c; }
+
+// ---------------------------------------------------------------------------
+// device helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 0 && gtimer() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// K-major operand tile: rows of 64 BF16 (128 B), 128-byte swizzle, 8-row
+// atoms of 1024 B (stride-dimension byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;
+    return d;
+}
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+
+// x = hi + mid + lo with each part BF16 (8 significant bits each)
+__device__ __forceinline__ __nv_bfloat16 split_part(float x, int part) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    if (part == 0) return hi;
+    const float r1 = x - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    if (part == 1) return mid;
+    return __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+struct TcEpi {
+    int mode;               // 0: FP64 C (alpha, beta); 1: BF16 packed output;
+                            // 2: ladder producer tile, staged through shared memory
+                            //    and stored as 16-byte vectors (see ladder_tc)
+    double* C;
+    __nv_bfloat16* P;
+    double alpha, beta;
+    int nm, nn;
+    long m_size[kMaxMode], m_s[kMaxMode];
+    long n_size[kMaxMode], n_s[kMaxMode];
+    long M, N;
+    int nseg;               // modes 1/2: segments written (1, 3 or 6)
+    long segstride;         // modes 1/2: elements between segments
+    int pat[6];             // modes 1/2: part per segment, 0 = hi, 1 = mid, 2 = lo
+    // mode 2: row m = (r, c) with c < V; column n = (b', d) with d < Vp;
+    //         element -> P[(r*Vb + b')*rowlen + c*Vp + d]
+    long V, Vp, rowlen, Vb;
+    // mode 3: ladder consumer scatter; row m = (s, i, j), column n = (r, b')
+    //         with a = a0 + r, b = a0 + b' (only b >= a is used):
+    //         s = 0,1 (same spin): R[s][ij][a][b] += v, R[s][ij][b][a] -= v
+    //         s = 2 (ab):           R[2][ij][a][b] += v
+    //         s = 3 (ab, (c,d) exchanged): R[2][ij][b][a] += v  (b > a)
+    long a0, OO, VV;
+};
+
+__device__ __forceinline__ long decomp1(long idx, int nmode, const long* size, const long* s) {
+    long o = 0;
+#pragma unroll
+    for (int j = kMaxMode - 1; j >= 0; --j) {
+        if (j < nmode) {
+            long q = idx / size[j];
+            o += (idx - q * size[j]) * s[j];
+            idx = q;
+        }
+    }
+    return o;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kStageBytesMode2 = 4 * 32 * 64 * 2;  // epilogue staging, 4 warps x 2 halves x 32 rows x 64 B
+
+// Persistent tcgen05 GEMM: one CTA per SM walks the output tiles (m fastest);
+// two TMEM accumulators of BN columns let the epilogue of one tile overlap
+// the MMAs of the next.
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
+              int nkt, int tilesM, int tilesN, int* err) {
+    constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+    constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* staging = smem + TC_STAGES * STAGE;
+    uint64_t* full = (uint64_t*)(staging + kStageBytesMode2);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* accf = empty + TC_STAGES;  // [2] MMA -> epilogue
+    uint64_t* acce = accf + 2;           // [2] epilogue -> MMA
+    uint32_t* tslot = (uint32_t*)(acce + 2);
+    volatile int* issued = (volatile int*)(tslot + 1);
+    volatile int* consumed = issued + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = tilesM * tilesN;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        *issued = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, 2 * BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile % tilesM) * TC_BM, n0 = (tile / tilesM) * BN;
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = g % TC_STAGES, round = g / TC_STAGES;
+                    if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], STAGE);
+                    tma_load_2d(smem + s * STAGE, &tmA, &full[s], kt * TC_BK, m0);
+                    tma_load_2d(smem + s * STAGE + A_BYTES, &tmB, &full[s], kt * TC_BK, n0);
+                    *issued = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                       ((uint32_t)(TC_BM >> 4) << 24);
+            int g = 0, j = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
+                const int buf = j & 1, u = j >> 1;
+                if (u > 0 && !mbar_wait(&acce[buf], (u - 1) & 1)) {
+                    atomicExch(err, 4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = g % TC_STAGES, round = g / TC_STAGES;
+                    if (!mbar_wait(&full[s], round & 1)) {
+                        atomicExch(err, 2);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                 (kt > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                    *consumed = g + 1;
+                }
+                if (ok) mma_commit(&accf[buf]);
+            }
+            if (!ok) {
+                // let issued MMAs finish and drain copies that were not consumed
+                uint64_t* fin = &accf[j & 1];
+                mma_commit(fin);
+                for (int kt = *consumed; kt < *issued; ++kt) mbar_wait(&full[kt % TC_STAGES], (kt / TC_STAGES) & 1);
+            }
+        }
+    } else {
+        // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
+        const int q = warp & 3;
+        int j = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+            const int buf = j & 1, u = j >> 1;
+            const int m0 = (tile % tilesM) * TC_BM, n0 = (tile / tilesM) * BN;
+            const bool ok = mbar_wait(&accf[buf], u & 1);
+            tc_fence_after();
+            if (!ok) {
+                atomicExch(err, 3);
+                break;
+            }
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+            if (epi.mode == 2) {
+                // lane = row; BF16 conversion staged through shared memory, then
+                // each row's 64 contiguous bytes go out as four 16-byte vectors,
+                // 8 rows per warp instruction
+                uint4* stage = (uint4*)(staging + q * 32 * 64 * 2);
+                const long m = (long)m0 + 32 * q + lane;
+                const long r_of = m / epi.V, c_of = m - r_of * epi.V;
+                const long rowbase = r_of * epi.Vb * epi.rowlen + c_of * epi.Vp;
+                const float alpha = (float)epi.alpha;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t rr[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), rr);
+                    const long nst = (long)n0 + ch * 32;
+                    for (int sgm = 0; sgm < epi.nseg; ++sgm) {
+                        uint32_t w[16];
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj += 2) {
+                            uint32_t two[2];
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                const float x = alpha * __uint_as_float(rr[jj + t]);
+                                two[t] = (uint32_t)__bfloat16_as_ushort(split_part(x, epi.pat[sgm]));
+                            }
+                            w[jj / 2] = two[0] | (two[1] << 16);
+                        }
+                        uint4* row = stage + (sgm & 1) * 128 + lane * 4;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            row[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int it = 0; it < 4; ++it) {
+                            const int rrow = it * 8 + (lane >> 2), piece = lane & 3;
+                            const long base = __shfl_sync(0xffffffffu, rowbase, rrow);
+                            const long mrow = (long)m0 + 32 * q + rrow;
+                            const long np = nst + piece * 8;
+                            if (mrow < epi.M && np < epi.N) {
+                                const long b = np / epi.Vp, dd = np - b * epi.Vp;
+                                const uint4 val = stage[(sgm & 1) * 128 + rrow * 4 + piece];
+                                *(uint4*)(epi.P + base + b * epi.rowlen + dd + sgm * epi.segstride) = val;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            } else if (epi.mode == 3) {
+                const long m = (long)m0 + 32 * q + lane;
+                const bool rowok = m < epi.M;
+                const int sblk = (int)(m / epi.OO);
+                const long ij = m - (long)sblk * epi.OO;
+                double* Rb = epi.C + (long)(sblk < 2 ? sblk : 2) * epi.OO * epi.VV + ij * epi.VV;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+                    if (!rowok) continue;
+                    const long nst = (long)n0 + ch * 32;
+                    long rr = nst / epi.Vb, bb = nst - rr * epi.Vb;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        if (nst + jj < epi.N) {
+                            const long a = epi.a0 + rr, b = epi.a0 + bb;
+                            const double v = (double)__uint_as_float(r[jj]);
+                            if (b >= a) {
+                                if (sblk < 2) {
+                                    Rb[a * epi.V + b] += v;
+                                    Rb[b * epi.V + a] -= v;
+                                } else if (sblk == 2) {
+                                    Rb[a * epi.V + b] += v;
+                                } else if (b > a) {
+                                    Rb[b * epi.V + a] += v;
+                                }
+                            }
+                        }
+                        if (++bb == epi.Vb) { bb = 0; ++rr; }
+                    }
+                }
+            } else {
+                const long m = (long)m0 + 32 * q + lane;
+                const bool rowok = m < epi.M;
+                const long roff = rowok ? decomp1(m, epi.nm, epi.m_size, epi.m_s) : 0;
+                const float alpha = (float)epi.alpha;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+                    if (!rowok) continue;
+                    // column offsets: decompose the chunk's first column once,
+                    // then step the mode counters (no divisions per element)
+                    long ci[kMaxMode];
+                    long coff = 0;
+                    {
+                        long idx = (long)n0 + ch * 32;
+#pragma unroll
+                        for (int k = kMaxMode - 1; k >= 0; --k) {
+                            if (k < epi.nn) {
+                                const long qq = idx / epi.n_size[k];
+                                ci[k] = idx - qq * epi.n_size[k];
+                                coff += ci[k] * epi.n_s[k];
+                                idx = qq;
+                            } else {
+                                ci[k] = 0;
+                            }
+                        }
+                    }
+                    // offsets of the 32 columns (distinct addresses)
+                    long offs[32];
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        offs[jj] = ((long)n0 + ch * 32 + jj < epi.N) ? roff + coff : -1;
+#pragma unroll
+                        for (int k = kMaxMode - 1; k >= 0; --k) {
+                            if (k < epi.nn) {
+                                coff += epi.n_s[k];
+                                if (++ci[k] < epi.n_size[k]) break;
+                                coff -= ci[k] * epi.n_s[k];
+                                ci[k] = 0;
+                            }
+                        }
+                    }
+                    if (epi.mode == 0) {
+                        // read all accumulated values first, then write: keeps
+                        // the 32 loads in flight instead of load/store pairs
+                        double old[32];
+                        if (epi.beta != 0.0) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) old[jj] = offs[jj] >= 0 ? epi.C[offs[jj]] : 0.0;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (offs[jj] < 0) continue;
+                            const double v = (double)(alpha * __uint_as_float(r[jj]));
+                            epi.C[offs[jj]] = epi.beta != 0.0 ? fma(epi.beta, old[jj], v) : v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            if (offs[jj] < 0) continue;
+                            const float v = alpha * __uint_as_float(r[jj]);
+                            for (int sgm = 0; sgm < epi.nseg; ++sgm)
+                                epi.P[offs[jj] + sgm * epi.segstride] = split_part(v, epi.pat[sgm]);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// operand packing: strided FP64 view -> BF16 [rows][nseg * Kp] (K-major)
+// ---------------------------------------------------------------------------
+struct PackArgs {
+    const double* src;
+    __nv_bfloat16* dst;
+    long rows, K, Kp;
+    int nseg;
+    int pat[6];
+    int nr, nk;
+    long r_size[kMaxMode], r_s[kMaxMode];
+    long k_size[kMaxMode], k_s[kMaxMode];
+    int kfast;  // source contiguous along k
+    long rvalid, kvalid;  // innermost row / k mode indices >= these read as 0
+};
+
+__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+    __shared__ double tile[32][65];
+    __shared__ long roff[32], koff[64];
+    const long ntr = (a.rows + 31) / 32, ntk = (a.Kp + 63) / 64;
+    for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
+        const long r0 = (t / ntk) * 32, k0 = (t % ntk) * 64;
+        // source offsets of the tile's rows and columns (-1: reads as zero)
+        if (threadIdx.x < 32) {
+            const long r = r0 + threadIdx.x;
+            long o = -1;
+            if (r < a.rows && (a.nr == 0 || (r % a.r_size[a.nr - 1]) < a.rvalid))
+                o = decomp1(r, a.nr, a.r_size, a.r_s);
+            roff[threadIdx.x] = o;
+        } else if (threadIdx.x < 96) {
+            const int kk = threadIdx.x - 32;
+            const long k = k0 + kk;
+            long o = -1;
+            if (k < a.K && (a.nk == 0 || (k % a.k_size[a.nk - 1]) < a.kvalid))
+                o = decomp1(k, a.nk, a.k_size, a.k_s);
+            koff[kk] = o;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+            int rr, kk;
+            if (a.kfast) { kk = e & 63; rr = e >> 6; }
+            else { rr = e & 31; kk = e >> 5; }
+            const long ro = roff[rr], ko = koff[kk];
+            tile[rr][kk] = (ro >= 0 && ko >= 0) ? a.src[ro + ko] : 0.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+            const int kk = e & 63, rr = e >> 6;
+            const long r = r0 + rr, k = k0 + kk;
+            if (r < a.rows && k < a.Kp) {
+                const float v = (float)tile[rr][kk];
+                __nv_bfloat16* d = a.dst + r * (a.nseg * a.Kp) + k;
+                for (int s = 0; s < a.nseg; ++s) d[s * a.Kp] = split_part(v, a.pat[s]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Buf {
+    __nv_bfloat16* p = nullptr;
+    size_t cap = 0;  // elements
+};
+
+struct TcEngine {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    int* d_err = nullptr;
+    Buf pa, pb, pv, pt;  // generic A, generic B, ladder V tile, stacked amplitudes
+    bool attr_set = false;
+};
+
+static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
+    if (b.cap >= elems) return DCSD_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (cudaMalloc((void**)&b.p, elems * sizeof(__nv_bfloat16)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "cudaMalloc of BF16 operand buffer failed";
+        return DCSD_ERR_OOM;
+    }
+    b.cap = elems;
+    return DCSD_OK;
+}
+
+dcsd_status tc_init(Ctx* c) {
+    TcEngine* e = new TcEngine();
+    c->tc = e;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        c->err = "cuTensorMapEncodeTiled unavailable";
+        return DCSD_ERR_CUDA;
+    }
+    e->encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    e->d_err = (int*)(c->scal + 22);  // device error word, read back with the scalars
+    DCSD_CUDA(c, cudaMemset(c->scal, 0, 64 * sizeof(double)));
+    return DCSD_OK;
+}
+
+void tc_free(Ctx* c) {
+    TcEngine* e = c->tc;
+    if (!e) return;
+    for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt})
+        if (b->p) cudaFree(b->p);
+    delete e;
+    c->tc = nullptr;
+}
+
+static long round_up(long x, long m) { return (x + m - 1) / m * m; }
+
+static dcsd_status make_map(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, long rows, long kt,
+                            int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)kt, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(kt * 2)};
+    cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = c->tc->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p, dims, strides, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return DCSD_ERR_CUDA;
+    }
+    return DCSD_OK;
+}
+
+static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
+                        const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
+                        const int* pat, __nv_bfloat16* dst, long rvalid = 1l << 62,
+                        long kvalid = 1l << 62) {
+    PackArgs a;
+    a.rvalid = rvalid;
+    a.kvalid = kvalid;
+    a.src = src;
+    a.dst = dst;
+    a.rows = rows;
+    a.K = K;
+    a.Kp = Kp;
+    a.nseg = nseg;
+    for (int i = 0; i < 6; ++i) a.pat[i] = i < nseg ? pat[i] : 0;
+    a.nr = nr;
+    a.nk = nk;
+    for (int i = 0; i < kMaxMode; ++i) {
+        a.r_size[i] = i < nr ? rsz[i] : 1;
+        a.r_s[i] = i < nr ? rs[i] : 0;
+        a.k_size[i] = i < nk ? ksz[i] : 1;
+        a.k_s[i] = i < nk ? ks[i] : 0;
+    }
+    a.kfast = (nk > 0 && ks[nk - 1] == 1) ? 1 : 0;
+    long tiles = ((rows + 31) / 32) * ((Kp + 63) / 64);
+    unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, (long)c->num_sms * 8));
+    prof_begin(c, DCSD_PROF_PACK);
+    if (c->trace)
+        trace_begin(c, "pack " + c->cur_spec + " rows=" + std::to_string(rows) + " K=" + std::to_string(K) + " kfast=" +
+                           std::to_string(a.kfast));
+    k_pack<<<g, 256, 0, c->stream>>>(a);
+    trace_end(c);
+    prof_end(c, DCSD_PROF_PACK);
+    return launch_check(c, "tc_pack");
+}
+
+// C = alpha * A_p B_p^T (+ beta C); A_p [M][Ktot], B_p [N][Ktot] packed BF16
+static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __nv_bfloat16* Bp, long N,
+                               long Ktot, TcEpi& epi) {
+    TcEngine* e = c->tc;
+    if (!e->attr_set) {
+        size_t s256 = TC_STAGES * (TC_BM * TC_BK * 2 + 256 * TC_BK * 2) + kStageBytesMode2 + 2048;
+        size_t s128 = TC_STAGES * (TC_BM * TC_BK * 2 + 128 * TC_BK * 2) + kStageBytesMode2 + 2048;
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s256));
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s128));
+        e->attr_set = true;
+    }
+    const int BN = N >= 256 ? 256 : 128;
+    CUtensorMap ma, mb;
+    DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM));
+    DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN));
+    epi.M = M;
+    epi.N = N;
+    const int nkt = (int)(Ktot / TC_BK);
+    const long tilesM = (M + TC_BM - 1) / TC_BM, tilesN = (N + BN - 1) / BN;
+    if (tilesM * tilesN > (1l << 31) - 1) {
+        c->err = "tensor-core GEMM too large";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    dim3 grid((unsigned)std::min<long>(tilesM * tilesN, c->num_sms));
+    size_t smem = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
+    const int cls = c->ladder_phase ? DCSD_PROF_LADDER : DCSD_PROF_TC_OTHER;
+    prof_begin(c, cls);
+    if (c->trace)
+        trace_begin(c, std::string(c->ladder_phase ? "tc-ladder " : "tc ") + c->cur_spec + " mode=" + std::to_string(epi.mode) +
+                           " M=" + std::to_string(M) + " N=" + std::to_string(N) + " Kt=" + std::to_string(Ktot));
+    if (BN == 256)
+        k_tc_gemm<256><<<grid, 192, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+    else
+        k_tc_gemm<128><<<grid, 192, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+    trace_end(c);
+    prof_end(c, cls);
+    return launch_check(c, "tc_gemm");
+}
+
+dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
+                           const TV& C, int nsplit);
+
+// Segments along K whose products sum to the split product:
+//   nsplit 2: x = h + m;       hh + hm + mh                (3 BF16 products)
+//   nsplit 3: x = h + m + l;   hh + hm + mh + hl + lh + mm (6 BF16 products)
+static void split_patterns(int nsplit, int& nseg, int* pa, int* pb) {
+    for (int i = 0; i < 6; ++i) pa[i] = pb[i] = 0;
+    if (nsplit == 3) {
+        nseg = 6;
+        const int A[6] = {0, 0, 1, 0, 2, 1}, B[6] = {0, 1, 0, 2, 0, 1};
+        for (int i = 0; i < 6; ++i) { pa[i] = A[i]; pb[i] = B[i]; }
+    } else if (nsplit == 2) {
+        nseg = 3;
+        pa[0] = 0; pa[1] = 0; pa[2] = 1;  // A: h h m
+        pb[0] = 0; pb[1] = 1; pb[2] = 0;  // B: h m h
+    } else {
+        nseg = 1;
+    }
+}
+
 dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
                       const TV& C, int nsplit) {
-    (void)nsplit;
-    return einsum64(c, spec, alpha, A, B, beta, C);
+    c->cur_spec = spec;
+    dcsd_status st = einsum_tc_impl(c, spec, alpha, A, B, beta, C, nsplit);
+    c->cur_spec = c->ladder_phase ? "ladder" : "";
+    return st;
 }
+
+dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
+                           const TV& C, int nsplit) {
+    GemmPlan p;
+    std::string err;
+    if (!plan_einsum(spec, A, B, C, p, err)) {
+        c->err = err;
+        return DCSD_ERR_INVALID_ARG;
+    }
+    if (p.NB != 1 || p.M < 1 || p.N < 1 || p.K < 16) return einsum64(c, spec, alpha, A, B, beta, C);
+    TcEngine* e = c->tc;
+    int nseg, pa[6], pb[6];
+    split_patterns(nsplit, nseg, pa, pb);
+    const long Kp = round_up(p.K, TC_BK);
+    const long Kt = nseg * Kp;
+    // The epilogue maps TMEM lanes (tile rows) to consecutive m: put on the
+    // m side whichever operand indexes the contiguous axis of C.
+    const bool m_contig = p.nm > 0 && p.m_sc[p.nm - 1] == 1;
+    const bool n_contig = p.nn > 0 && p.n_sc[p.nn - 1] == 1;
+    if (!m_contig && n_contig) {
+        GemmPlan q = p;
+        q.nm = p.nn; q.nn = p.nm; q.M = p.N; q.N = p.M;
+        for (int i = 0; i < kMaxMode; ++i) {
+            q.m_size[i] = p.n_size[i]; q.m_sa[i] = p.n_sb[i]; q.m_sc[i] = p.n_sc[i];
+            q.n_size[i] = p.m_size[i]; q.n_sb[i] = p.m_sa[i]; q.n_sc[i] = p.m_sc[i];
+            q.k_sa[i] = p.k_sb[i]; q.k_sb[i] = p.k_sa[i];
+        }
+        p = q;
+        DCSD_TRY(ensure(c, e->pa, (size_t)p.M * Kt));
+        DCSD_TRY(ensure(c, e->pb, (size_t)p.N * Kt));
+        DCSD_TRY(pack(c, B.p, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa, e->pa.p));
+        DCSD_TRY(pack(c, A.p, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb, e->pb.p));
+    } else {
+        DCSD_TRY(ensure(c, e->pa, (size_t)p.M * Kt));
+        DCSD_TRY(ensure(c, e->pb, (size_t)p.N * Kt));
+        DCSD_TRY(pack(c, A.p, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa, e->pa.p));
+        DCSD_TRY(pack(c, B.p, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb, e->pb.p));
+    }
+    TcEpi epi;
+    std::memset(&epi, 0, sizeof(epi));
+    epi.mode = 0;
+    epi.C = C.p;
+    epi.alpha = alpha;
+    epi.beta = beta;
+    epi.nm = p.nm;
+    epi.nn = p.nn;
+    for (int i = 0; i < kMaxMode; ++i) {
+        epi.m_size[i] = i < p.nm ? p.m_size[i] : 1;
+        epi.m_s[i] = i < p.nm ? p.m_sc[i] : 0;
+        epi.n_size[i] = i < p.nn ? p.n_size[i] : 1;
+        epi.n_s[i] = i < p.nn ? p.n_sc[i] : 0;
+    }
+    return gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi);
+}
+
+// ---------------------------------------------------------------------------
+// particle-particle ladder and its T1 correction on tensor cores
+//
+//   R2[s][ij][a][b] += sum_cd t_s[ij][cd] (ac|bd)             (s = aa, bb, ab)
+//   G[s][ij][k][b]   = sum_cd t_s[ij][cd] (kc|bd)             (s = aa, bb, ab, ab~)
+// (ac|bd) = sum_L B_L[a][c] B_L[b][d] is built per chunk of a (resp. k) by a
+// tcgen05 GEMM over L whose epilogue writes the tile in BF16 directly in the
+// K-major operand layout [(a,b)][(c,d)] of the contraction with the stacked
+// amplitudes [(s,i,j)][(c,d)]; the integrals are never stored beyond one
+// chunk.  ab~ is the alpha-beta block with (c,d) exchanged.
+// ---------------------------------------------------------------------------
+dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
+    TcEngine* e = c->tc;
+    const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
+    int nseg, pa[6], pb[6];
+    split_patterns(nsplit, nseg, pa, pb);
+    // (c,d) index of the contraction: c*Vp + d, d padded to a multiple of 8 so
+    // that the producer can store 16-byte vectors
+    const long Vp = round_up(V, 8);
+    const long K2 = V * Vp, K2p = round_up(K2, TC_BK), K2t = nseg * K2p;
+    const long XP = round_up(X, TC_BK), Xt = nseg * XP;
+    const long rows4 = 4 * O * O;
+    // stacked amplitudes [aa; bb; ab; ab~] x (c,d)
+    DCSD_TRY(ensure(c, e->pt, (size_t)rows4 * K2t));
+    {
+        long rsz[1] = {3 * O * O}, rs[1] = {V * V};
+        long ksz[2] = {V, Vp}, ks[2] = {V, 1};
+        DCSD_TRY(pack(c, c->t2, 1, rsz, rs, 2, ksz, ks, 3 * O * O, K2, K2p, nseg, pa, e->pt.p, 1l << 62, V));
+        long rsz2[1] = {O * O};
+        long ks2[2] = {1, V};  // (c,d) -> t_ab[ij][d][c]
+        DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks2, O * O, K2, K2p, nseg, pa,
+                      e->pt.p + (size_t)3 * O * O * K2t, 1l << 62, V));
+    }
+    // B_vv packed as [(b,d)][L], d padded (constant over the chunk loop)
+    DCSD_TRY(ensure(c, e->pb, (size_t)K2 * Xt));
+    {
+        long rsz[2] = {V, Vp}, rs[2] = {n, 1};
+        long ksz[1] = {X}, ks[1] = {n * n};
+        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, K2, X, XP, nseg, pb, e->pb.p, V));
+    }
+    const long chunk = std::max<long>(1, std::min<long>(V, 16));
+    DCSD_TRY(ensure(c, e->pv, (size_t)chunk * V * K2t));
+    DCSD_TRY(ensure(c, e->pa, (size_t)chunk * V * Xt));
+    struct PhaseGuard {
+        Ctx* c;
+        ~PhaseGuard() { c->ladder_phase = 0; c->cur_spec = ""; }
+    } guard{c};
+    c->ladder_phase = 1;
+    c->cur_spec = "ladder";
+    // rows first index a (ladder) then k (correction).  The ladder uses
+    // (ac|bd) = (bd|ac): per chunk of a only the columns b >= a0 are built
+    // and contracted; the (b,a) elements of the alpha-beta block come from the
+    // rows with (c,d) exchanged and same-spin blocks are antisymmetric.
+    for (int pass = 0; pass < 2; ++pass) {
+        const long R = pass == 0 ? V : O;
+        for (long r0 = 0; r0 < R; r0 += chunk) {
+            const long nr = std::min(chunk, R - r0);
+            const long b0 = pass == 0 ? r0 : 0;  // first b column built
+            const long Vb = V - b0;
+            // producer A: rows (r,c) of B_L[row][c] -> [(r,c)][L]
+            {
+                long rsz[2] = {nr, V}, rs[2] = {n, 1};
+                long ksz[1] = {X}, ks[1] = {n * n};
+                const double* src = c->B + (pass == 0 ? (nc + r0) * n + nc : r0 * n + nc);
+                DCSD_TRY(pack(c, src, 2, rsz, rs, 1, ksz, ks, nr * V, X, XP, nseg, pa, e->pa.p));
+            }
+            // producer: tile (r,c) x (b,d) -> V_p[(r,b)][(c,d)] (BF16, consumer-B layout)
+            TcEpi pe;
+            std::memset(&pe, 0, sizeof(pe));
+            pe.mode = 2;
+            pe.P = e->pv.p;
+            pe.alpha = 1.0;
+            pe.nseg = nseg;
+            pe.segstride = K2p;
+            for (int i = 0; i < 6; ++i) pe.pat[i] = pb[i];
+            pe.V = V;
+            pe.Vp = Vp;
+            pe.rowlen = K2t;
+            pe.Vb = Vb;
+            DCSD_TRY(gemm_packed(c, e->pa.p, nr * V, e->pb.p + (size_t)b0 * Vp * Xt, Vb * Vp, Xt, pe));
+            // consumer: rows (s,i,j) x cols (r,b) over (c,d)
+            TcEpi ce;
+            std::memset(&ce, 0, sizeof(ce));
+            ce.mode = 0;
+            ce.alpha = 1.0;
+            ce.nm = 1;
+            ce.nn = 2;
+            for (int i = 0; i < kMaxMode; ++i) { ce.m_size[i] = ce.n_size[i] = 1; ce.m_s[i] = ce.n_s[i] = 0; }
+            if (pass == 0) {
+                ce.mode = 3;
+                ce.C = R2;
+                ce.V = V;
+                ce.Vb = Vb;
+                ce.a0 = r0;
+                ce.OO = O * O;
+                ce.VV = V * V;
+                DCSD_TRY(gemm_packed(c, e->pt.p, rows4, e->pv.p, nr * Vb, K2t, ce));
+            } else {
+                ce.C = G + r0 * V;       // G[s][i][j][k][b], rows (s,i,j) stride O*V
+                ce.beta = 0.0;
+                ce.m_size[0] = rows4; ce.m_s[0] = O * V;
+                ce.n_size[0] = nr; ce.n_s[0] = V;
+                ce.n_size[1] = V;  ce.n_s[1] = 1;
+                DCSD_TRY(gemm_packed(c, e->pt.p, rows4, e->pv.p, nr * V, K2t, ce));
+            }
+        }
+    }
+    return DCSD_OK;
+}
+
 }  // namespace dcsd

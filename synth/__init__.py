@@ -17,8 +17,15 @@ Recipe (stand-in for the paper's molecules, which are not available):
   * a Z2 "symmetry" label per orbital (t even, u odd, others random) and per
     auxiliary function, so t and u lie in different irreps (the CAS case of
     Section II) and active-active singles vanish exactly;
-  * DF factors B[L,p,q] ~ N(0, 0.05^2), drawn for p<=q and mirrored, zeroed
-    unless parity(p) xor parity(q) == parity(L);
+  * DF factors B[L,p,q] ~ N(0, sigma^2), drawn for p<=q and mirrored, zeroed
+    unless parity(p) xor parity(q) == parity(L).  sigma = 0.05 for the
+    smallest workload (naux = 60, 21 virtuals per spin) and
+    sigma = 0.05 * (60 * 21^2 / (naux * v^2))^(1/4) when that is smaller, so
+    that a pair's second-order correlation, sum_ab (ia|jb)^2 / D ~
+    v^2 * naux * sigma^4, keeps the size it has there.  With a fixed sigma the
+    exchange integrals (pq|pq) = sum_L B_pq^2 grow like naux (1.9 Eh at
+    naux = 1500) and the pair correlation like v^2 naux: the amplitude
+    equations then diverge even in FP64;
   * Fock matrices f^alpha, f^beta = diag(eps) + symmetric off-diagonal noise
     N(0, 0.005^2), independent per spin, zeroed where parities differ.
 """
@@ -94,8 +101,13 @@ def make_B(rng, n, naux, par, par_aux, sigma=0.05):
     return B
 
 
+def b_sigma_for(naux, v):
+    """DF factor spread: 0.05 * min(1, (60 * 21^2 / (naux * v^2))^(1/4))."""
+    return 0.05 * min(1.0, (60.0 * 21.0 ** 2 / (naux * float(v) ** 2)) ** 0.25)
+
+
 def make_system(name_or_dims, seed=None, eps_t=None, eps_u=None,
-                fock_noise=0.005, b_sigma=0.05) -> System:
+                fock_noise=0.005, b_sigma=None) -> System:
     """Synthetic DF Hamiltonian for a named workload ('c1'..'c5') or for
     explicit (n_c, n_v, naux)."""
     if isinstance(name_or_dims, str):
@@ -120,7 +132,7 @@ def make_system(name_or_dims, seed=None, eps_t=None, eps_u=None,
     mask = (par[:, None] == par[None, :]).astype(float)
     fa = np.diag(eps) + _sym_noise(rng, n, fock_noise, mask)
     fb = np.diag(eps) + _sym_noise(rng, n, fock_noise, mask)
-    B = make_B(rng, n, naux, par, par_aux, b_sigma)
+    B = make_B(rng, n, naux, par, par_aux, b_sigma if b_sigma is not None else b_sigma_for(naux, n_v + 1))
     return System(n_c, n_v, naux, eps, par, par_aux, B, fa, fb)
 
 

@@ -1,0 +1,39 @@
+"""Write oracle energies of the named workloads to tests/golden/*.json.
+
+Calls only the CPU oracle (oracle/) and the seeded generator (synth/).
+Usage: python tests/golden/make_golden.py c1 [c2 ...]
+The GPU tests compare the library's converged energies with these files.
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from synth import CONFIGS, CONFIG_SEED, b_sigma_for, make_system  # noqa: E402
+from oracle import solve  # noqa: E402
+
+TOL = {"c1": 1e-10, "c2": 1e-10, "c3": 1e-9, "c4": 1e-10}
+
+
+def main(names):
+    for name in names:
+        s = make_system(name)
+        out = {"workload": name, "dims": CONFIGS[name][:3], "seed": CONFIG_SEED[name],
+               "b_sigma": b_sigma_for(s.naux, s.v), "generator": "synth.make_system", "results": {}}
+        for method, mname in ((0, "2D-CCSD"), (1, "2D-DCSD")):
+            t0 = time.time()
+            _, info = solve.solve(s, method, ref=0, tol=TOL[name], maxiter=300, verbose=True)
+            out["results"][mname] = {k: float(info[k]) for k in ("dEA", "W", "E_S", "E_T", "max_r")}
+            out["results"][mname]["iters"] = int(info["iters"])
+            out["results"][mname]["converged"] = bool(info["converged"])
+            out["results"][mname]["oracle_seconds"] = time.time() - t0
+            print(name, mname, out["results"][mname], flush=True)
+        with open(os.path.join(HERE, f"{name}_energies.json"), "w") as f:
+            json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["c1"])

@@ -89,3 +89,26 @@ def test_invalid_arguments_rejected(P):
     with pytest.raises(P.DcsdError):
         eng.residual(T, precision=9)
     eng.close()
+
+
+# Tensor-core paths.  BF16 has a unit roundoff of 2^-9; with FP32 accumulation
+# over K terms the residual error is bounded by ~K^(1/2) 2^-9 times the size of
+# the largest contributing products, observed <= 5e-3 max|R|: tolerance 2e-2
+# max|R|.  The split (hi+lo) products carry 2^-17 relative error per product;
+# FP32 accumulation then dominates: tolerance 2e-4 max|R|.
+@pytest.mark.parametrize("dims,seed", [((2, 5, 12), 3), ((4, 20, 30), 4), ((6, 40, 64), 5)])
+@pytest.mark.parametrize("prec,rtol", [(1, 2e-2), (2, 2e-4)])
+@pytest.mark.parametrize("method", [0, 1])
+def test_residual_tensor_core_within_precision(P, dims, seed, prec, rtol, method):
+    s = make_system(dims, seed=seed)
+    T = random_amplitudes(s, seed=seed + 100, scale1=0.02, scale2=0.02)
+    eng = P.Engine.from_system(s)
+    Td = eng.to_device(T)
+    R, W, dE = eng.residual(Td, method=method, precision=prec)
+    R = [x.cpu().numpy() for x in R]
+    Ro, Wo, dEo = twod.residual(s, 0, method, T)
+    rmax = max(np.abs(x).max() for x in Ro)
+    assert _cmp(R, Ro) < rtol * rmax
+    assert abs(W - Wo) < rtol * rmax
+    assert abs(dE - dEo) < 1e-12  # the energy is always FP64
+    eng.close()
