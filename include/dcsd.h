@@ -201,6 +201,33 @@ typedef enum {
 dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
                          long long* launches);
 
+/* dcsd_energy_noalloc -- Delta E_A (the first term of Eq. 2, as returned by
+ * dcsd_energy) for callers that cannot allocate device memory: code that is
+ * capturing a CUDA graph, that hands all device memory to its own pool
+ * allocator, or that must keep a fixed footprint.  The paper has no
+ * counterpart; this is a service of the library.
+ *   n_c, n_v, naux, ref : as for dcsd_init / dcsd_residual.
+ *   fock_a, fock_b, B   : device pointers, layouts of dcsd_init.
+ *   T1a .. T2ab         : device pointers, amplitude layout of this header.
+ *   dEA                 : device pointer receiving one double.
+ *   stream              : cudaStream_t the two kernels are enqueued on; the
+ *                         call does not synchronise it.
+ * Allocates nothing: its only working memory is a fixed device array that
+ * is part of the library (8192 doubles, one partial sum per spin block and
+ * occupied pair), so n_c + 1 must not exceed 52 (else INVALID_ARG).  The
+ * array is shared by all calls and keeps the last call's contents: calls
+ * that overlap on the GPU race and must be serialised by the caller.  The
+ * first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture begins.
+ * Errors: INVALID_ARG (NULL pointer, sizes beyond the limit), NO_DEVICE,
+ * CUDA (launch failure). */
+dcsd_status dcsd_energy_noalloc(int n_c, int n_v, int naux, int ref,
+                                const double* fock_a, const double* fock_b,
+                                const double* B, const double* T1a,
+                                const double* T1b, const double* T2aa,
+                                const double* T2bb, const double* T2ab,
+                                double* dEA, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
-           "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile"]
+           "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
+           "dcsd_energy_noalloc"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -72,6 +73,8 @@ def load():
     lib.dcsd_kernel_launches.restype = C.c_longlong
     lib.dcsd_profile.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     lib.dcsd_profile.restype = C.c_int
+    lib.dcsd_energy_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10
+    lib.dcsd_energy_noalloc.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -145,3 +148,10 @@ def dcsd_profile(ctx, enable, reset, read=True):
     if not read:
         return None
     return {PROF_CLASSES[k]: (ms[k], ln[k]) for k in range(8)}
+
+
+def dcsd_energy_noalloc(n_c, n_v, naux, ref, fock_a, fock_b, B, T, dEA, stream):
+    """Allocation-free Delta E_A; all pointers are device addresses (ints)."""
+    st = load().dcsd_energy_noalloc(n_c, n_v, naux, ref, fock_a, fock_b, B, *T, dEA, stream)
+    if st != DCSD_OK:
+        raise DcsdError(st, "dcsd_energy_noalloc failed")
