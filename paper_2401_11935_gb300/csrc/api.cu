@@ -20,38 +20,76 @@ namespace dcsd {
 // step = -R / D with D the Fock-diagonal orbital-energy differences of the
 // frame (zero where R is zero: padding, masked and symmetry-forbidden
 // elements); tnew = t + step.
-__global__ void k_jacobi(int n, int nc, int O, int V, const double* fa, const double* fb,
-                         const double* t, const double* R, double* tnew, double* step) {
-    const long n1 = 2l * O * V, nb = (long)O * O * V * V, total = n1 + 3 * nb;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-         e += (long)gridDim.x * blockDim.x) {
-        double r = R[e], st = 0.0;
-        if (r != 0.0) {
-            double D;
-            if (e < n1) {
-                int s = (int)(e / ((long)O * V));
-                int i = (int)((e / V) % O), a = (int)(e % V);
-                const double* f = s == 0 ? fa : fb;
-                D = f[(long)(nc + a) * n + nc + a] - f[(long)i * n + i];
-            } else {
-                long r2 = e - n1;
-                int blk = (int)(r2 / nb);
-                r2 -= blk * nb;
-                int b = (int)(r2 % V);
-                r2 /= V;
-                int a = (int)(r2 % V);
-                r2 /= V;
-                int j = (int)(r2 % O);
-                int i = (int)(r2 / O);
-                const double* f1 = blk == 1 ? fb : fa;
-                const double* f2 = blk == 0 ? fa : fb;
-                D = f1[(long)(nc + a) * n + nc + a] + f2[(long)(nc + b) * n + nc + b] -
-                    f1[(long)i * n + i] - f2[(long)j * n + j];
-            }
-            st = -r / D;
+// 1/D for the Jacobi step: FP32 reciprocal refined by one Newton-Raphson
+// iteration r <- r (2 - D r) in FP64 (relative error about 2^-46), a few FP64
+// operations instead of a full-precision division
+__device__ __forceinline__ double recip_nr(double D) {
+    double r = (double)__frcp_rn((float)D);
+    return fma(r, fma(-D, r, 1.0), r);
+}
+
+// Jacobi step on the concatenated amplitude vector: one block per row --
+// 2*O rows of T1 (length V), then 3*O*O rows of T2 (length V*V).  The
+// virtual diagonal Fock elements of the row's spins are staged in shared
+// memory (2*V doubles of dynamic shared memory, or read from the Fock
+// matrices when stage is false).
+__global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V, const double* fa,
+                                                     const double* fb, const double* t, const double* R,
+                                                     double* tnew, double* step, bool stage) {
+    extern __shared__ double jdiag[];  // [2][V]
+    const long nrow1 = 2l * O, nrow = nrow1 + 3l * O * O;
+    for (long row = blockIdx.x; row < nrow; row += gridDim.x) {
+        int blk, i, j;
+        if (row < nrow1) {
+            blk = (int)(row / O);  // spin of the T1 row
+            i = (int)(row % O);
+            j = -1;
+        } else {
+            const long r2 = row - nrow1;
+            blk = (int)(r2 / ((long)O * O));
+            i = (int)((r2 / O) % O);
+            j = (int)(r2 % O);
         }
-        step[e] = st;
-        tnew[e] = t[e] + st;
+        const bool is1 = j < 0;
+        const double* f1 = is1 ? (blk == 0 ? fa : fb) : (blk == 1 ? fb : fa);
+        const double* f2 = is1 ? f1 : (blk == 0 ? fa : fb);
+        const double* d1 = f1 + (long)nc * n + nc;  // diagonal, stride n + 1
+        const double* d2 = f2 + (long)nc * n + nc;
+        long d1s = n + 1, d2s = n + 1;
+        if (stage) {
+            __syncthreads();  // previous row done with the staged diagonal
+            for (int x = threadIdx.x; x < V; x += blockDim.x) {
+                jdiag[x] = d1[(long)x * (n + 1)];
+                jdiag[V + x] = d2[(long)x * (n + 1)];
+            }
+            __syncthreads();
+            d1 = jdiag;
+            d2 = jdiag + V;
+            d1s = d2s = 1;
+        }
+        if (is1) {
+            const long base = row * V;
+            const double dij = f1[(long)i * n + i];
+            for (int x = threadIdx.x; x < V; x += blockDim.x) {
+                const double r = R[base + x];
+                const double st = r != 0.0 ? -r * recip_nr(d1[x * d1s] - dij) : 0.0;
+                step[base + x] = st;
+                tnew[base + x] = t[base + x] + st;
+            }
+        } else {
+            const long base = 2l * O * V + (row - nrow1) * V * V;
+            const double dij = f1[(long)i * n + i] + f2[(long)j * n + j];
+            for (int x = 0; x < V; ++x) {
+                const double Da = d1[x * d1s] - dij;
+                const long rb = base + (long)x * V;
+                for (int b = threadIdx.x; b < V; b += blockDim.x) {
+                    const double r = R[rb + b];
+                    const double st = r != 0.0 ? -r * recip_nr(Da + d2[b * d2s]) : 0.0;
+                    step[rb + b] = st;
+                    tnew[rb + b] = t[rb + b] + st;
+                }
+            }
+        }
     }
 }
 
@@ -275,7 +313,7 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
     A_(c->big1, c->big_elems);
     A_(c->big2, c->big_elems);
     A_(c->big3, c->big_elems);
-    A_(c->red, 1024);
+    A_(c->red, kRedDoubles);
     c->splitk_elems = std::max<size_t>(1 << 20, std::min<size_t>(64ul << 20, 16 * (n * n + O * V)));
     A_(c->splitk_ws, c->splitk_elems);
     A_(c->scal, 64);
@@ -561,8 +599,15 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         }
         double* st_v = nd > 0 ? c->diis_e + (size_t)next * len : sbuf;
         double* tn_v = nd > 0 ? c->diis_t + (size_t)next * len : tbuf;
-        k_jacobi<<<grid_n(c, len), 256, 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, c->t1, c->R1,
-                                                        tn_v, st_v);
+        trace_begin(c, "jacobi");
+        {
+            const size_t jsm = 2ul * c->V * sizeof(double);
+            const bool stage = jsm <= 48 * 1024;
+            k_jacobi_rows<<<(unsigned)std::min<long>(2l * c->O + 3l * c->O * c->O, (long)c->num_sms * 8), 256,
+                            stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, c->t1, c->R1, tn_v,
+                                                          st_v, stage);
+        }
+        trace_end(c);
         if ((s = launch_check(c, "jacobi")) != DCSD_OK) { status = s; break; }
         if (nd == 0) {
             DCSD_CUDA(c, cudaMemcpyAsync(c->t1, tn_v, len * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -573,13 +618,11 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         next = (next + 1) % nd;
         nhist = std::min(nhist + 1, nd);
         // new row of the DIIS matrix
-        TV ev = view(st_v, {len});
-        for (int j = 0; j < nhist; ++j) {
-            int sl = (cur - j + nd) % nd;
-            if ((s = dot_view(c, ev, view(c->diis_e + (size_t)sl * len, {len}), c->scal + 24 + j, 0.0)) !=
-                DCSD_OK) { status = s; break; }
+        {
+            const double* ys[16];
+            for (int j = 0; j < nhist; ++j) ys[j] = c->diis_e + (size_t)((cur - j + nd) % nd) * len;
+            if ((s = multidot(c, st_v, ys, nhist, len, c->scal + 24)) != DCSD_OK) { status = s; break; }
         }
-        if (s != DCSD_OK) break;
         DCSD_CUDA(c, cudaMemcpyAsync(c->hostbuf + 24, c->scal + 24, sizeof(double) * nhist,
                                      cudaMemcpyDeviceToHost, c->stream));
         DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -614,7 +657,9 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
             lc.coef[0] = 1.0;
             lc.m = 1;
         }
+        trace_begin(c, "diis_lincomb");
         k_lincomb<<<grid_n(c, len), 256, 0, c->stream>>>(lc, len, c->t1);
+        trace_end(c);
         if ((s = launch_check(c, "diis_extrapolate")) != DCSD_OK) { status = s; break; }
     }
     if (sbuf) cudaFree(sbuf);

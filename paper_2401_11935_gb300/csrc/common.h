@@ -55,6 +55,9 @@ bool plan_einsum(const char* spec, const TV& A, const TV& B, const TV& C,
 struct MTables;   // two-determinant coupling tables (mterm.cu)
 struct TcEngine;  // tensor-core contraction engine (tc_gemm.cu)
 
+// reduction scratch (Ctx::red), in doubles
+constexpr int kRedDoubles = 16384;
+
 struct Ctx {
     int nc = 0, nv = 0, X = 0;
     int n = 0, O = 0, V = 0;      // n = nc+2+nv; union occ O = nc+2; union vir V = nv+2
@@ -147,6 +150,10 @@ dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& 
 // sum_i A_i * B_i over identical shapes -> *out (device pointer), FP64
 dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accumulate);
 dcsd_status fill(Ctx* c, double* p, size_t n, double val);
+// C += sum_k alpha_k A_k over up to 4 rank-4 views (one pass)
+dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C);
+// out[k] = <x, ys[k]> for k < m <= 16, contiguous vectors of length n (device out)
+dcsd_status multidot(Ctx* c, const double* x, const double* const* ys_host, int m, long n, double* out);
 
 // layout conversion between the ABI and the union layout
 dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b,
@@ -161,7 +168,8 @@ dcsd_status check_finite(Ctx* c, const double* p, size_t n, double* flag);
 // two-determinant layer
 dcsd_status mtables_build(Ctx* c);
 void mtables_free(Ctx* c);
-dcsd_status apply_mterms(Ctx* c, int ref);
+// coupling terms; fp32 = evaluate the doubles coefficient products in FP32
+dcsd_status apply_mterms(Ctx* c, int ref, bool fp32);
 
 // residual orchestration (residual.cu)
 dcsd_status residual_union(Ctx* c, int ref, int method, int precision);

@@ -526,8 +526,135 @@ dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& 
     a.C = C.p;
     a.alpha = alpha;
     a.beta = beta;
+    if (c->trace) trace_begin(c, "axpy rank=" + std::to_string(a.rank) + " n=" + std::to_string(a.total));
     k_axpy_view<<<grid_for(c, a.total), 256, 0, c->stream>>>(a);
+    trace_end(c);
     return launch_check(c, "axpy_view");
+}
+
+// C[i0,i1,i2,i3] += sum_k alpha_k * A_k[i0,i1,i2,i3] for up to 4 strided views
+// (rank 4); one pass over C.  Rows (i0,i1) per block, (i2,i3) per thread.
+struct Axpy4Args {
+    int nv;
+    long size[4];
+    long sc[4];
+    long sa[4][4];
+    const double* A[4];
+    double alpha[4];
+    double* C;
+};
+
+__global__ void __launch_bounds__(256) k_axpy4(Axpy4Args a) {
+    const long nrow = a.size[0] * a.size[1], ncol = a.size[2] * a.size[3];
+    for (long row = blockIdx.x; row < nrow; row += gridDim.x) {
+        const long i0 = row / a.size[1], i1 = row - i0 * a.size[1];
+        long rb[4];
+        for (int k = 0; k < 4; ++k) rb[k] = i0 * a.sa[k][0] + i1 * a.sa[k][1];
+        const long cb = i0 * a.sc[0] + i1 * a.sc[1];
+        for (long e = threadIdx.x; e < ncol; e += blockDim.x) {
+            const long i2 = e / a.size[3], i3 = e - i2 * a.size[3];
+            double v = a.C[cb + i2 * a.sc[2] + i3 * a.sc[3]];
+            for (int k = 0; k < a.nv; ++k) v += a.alpha[k] * a.A[k][rb[k] + i2 * a.sa[k][2] + i3 * a.sa[k][3]];
+            a.C[cb + i2 * a.sc[2] + i3 * a.sc[3]] = v;
+        }
+    }
+}
+
+dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C) {
+    Axpy4Args a;
+    if (C.rank != 4 || nv < 1 || nv > 4) {
+        c->err = "axpy4 needs rank-4 views";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    a.nv = nv;
+    for (int d = 0; d < 4; ++d) { a.size[d] = C.size[d]; a.sc[d] = C.stride[d]; }
+    for (int k = 0; k < 4; ++k) {
+        a.A[k] = k < nv ? A[k].p : C.p;
+        a.alpha[k] = k < nv ? alpha[k] : 0.0;
+        for (int d = 0; d < 4; ++d) {
+            if (k < nv && (A[k].rank != 4 || A[k].size[d] != C.size[d])) {
+                c->err = "axpy4 shape mismatch";
+                return DCSD_ERR_INVALID_ARG;
+            }
+            a.sa[k][d] = k < nv ? A[k].stride[d] : 0;
+        }
+    }
+    a.C = C.p;
+    const long nrow = C.size[0] * C.size[1];
+    if (c->trace) trace_begin(c, "axpy4 n=" + std::to_string(nrow * C.size[2] * C.size[3]));
+    k_axpy4<<<(unsigned)std::max<long>(1, std::min<long>(nrow, (long)c->num_sms * 32)), 256, 0, c->stream>>>(a);
+    trace_end(c);
+    return launch_check(c, "axpy4");
+}
+
+// dots of one vector with up to 16 others in a single pass (contiguous)
+struct MultiDotArgs {
+    const double* x;
+    const double* y[16];
+    int m;
+    long n;
+    double* partial;  // [m][gridDim.x]
+};
+
+__global__ void __launch_bounds__(256) k_multidot_partial(MultiDotArgs a) {
+    __shared__ double sh[8][16];
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.n; e += (long)gridDim.x * blockDim.x) {
+        const double xv = a.x[e];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < a.m) acc[k] = fma(xv, a.y[k][e], acc[k]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k >= a.m) break;
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < a.m) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sh[w][threadIdx.x];
+        a.partial[(long)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_multidot_final(const double* partial, int nblk, int m, double* out) {
+    const int k = blockIdx.x;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 256) s += partial[(long)k * nblk + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+}
+
+dcsd_status multidot(Ctx* c, const double* x, const double* const* ys_host, int m, long n, double* out) {
+    if (m < 1 || m > 16) {
+        c->err = "multidot supports 1..16 vectors";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    MultiDotArgs a;
+    a.x = x;
+    for (int k = 0; k < 16; ++k) a.y[k] = k < m ? ys_host[k] : x;
+    a.m = m;
+    a.n = n;
+    a.partial = c->red;
+    // 4 blocks per SM, partials m * nblk <= kRedDoubles
+    const int nblk = std::max(1, std::min(4 * std::max(c->num_sms, 1), kRedDoubles / 16));
+    trace_begin(c, "multidot");
+    k_multidot_partial<<<nblk, 256, 0, c->stream>>>(a);
+    k_multidot_final<<<m, 256, 0, c->stream>>>(c->red, nblk, m, out);
+    trace_end(c);
+    return launch_check(c, "multidot");
 }
 
 // deterministic two-pass dot product
@@ -574,7 +701,9 @@ dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accum
     if (!ew_setup(c, A, B, a)) return DCSD_ERR_INVALID_ARG;
     a.A = A.p;
     a.C = nullptr;
+    if (c->trace) trace_begin(c, "dot n=" + std::to_string(a.total));
     k_dot_partial<<<kDotBlocks, 256, 0, c->stream>>>(a, B.p, c->red);
+    trace_end(c);
     DCSD_TRY(launch_check(c, "dot_partial"));
     k_dot_final<<<1, 256, 0, c->stream>>>(c->red, kDotBlocks, out, accumulate);
     return launch_check(c, "dot_final");
@@ -657,9 +786,11 @@ dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b, cons
     DCSD_CUDA(c, cudaMemsetAsync(c->t2, 0, n2 * sizeof(double), c->stream));
     LayoutArgs L = layout_args(c, ref);
     long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
+    trace_begin(c, "layout");
     k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 0, c->t1, c->t2, (double*)T1a,
                                                           (double*)T1b, (double*)T2aa,
                                                           (double*)T2bb, (double*)T2ab);
+    trace_end(c);
     return launch_check(c, "unpack_T");
 }
 

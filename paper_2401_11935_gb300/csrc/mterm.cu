@@ -287,6 +287,10 @@ static dcsd_status derive_tables(Ctx* c, int ref, MTables& mt) {
             if (ok) mt.terms.push_back(m);
         }
         mt.cnt[cls] = (int)mt.terms.size() - mt.off[cls];
+        if (mt.cnt[cls] > 64) {
+            c->err = "two-determinant class with more than 64 terms";
+            return DCSD_ERR_INVALID_ARG;
+        }
         return DCSD_OK;
     };
 
@@ -309,6 +313,56 @@ static dcsd_status derive_tables(Ctx* c, int ref, MTables& mt) {
     return DCSD_OK;
 }
 
+// Largest number of distinct a-only factors / joint (a,b) factors over the
+// doubles classes whose a and b are external virtuals (set by mtables_build).
+static int g_max_xfac = 0, g_max_hfac = 0;
+
+// In a class with a and b both external, every term has exactly one factor
+// holding a and one holding b (each particle index occurs once in a product
+// of cluster amplitudes), so a term is either separable -- f(a) g(b) times
+// scalars -- or one factor h(a,b) times scalars.  Check that and count the
+// distinct symbolic a-factors and (a,b)-factors per class.
+static dcsd_status check_separable(Ctx* c, const MTables& mt) {
+    for (int blk = 0; blk < 3; ++blk)
+        for (int bits = 0; bits < 16; bits += 4) {
+            const int cls = blk * 16 + bits;
+            std::vector<MFac> xs, hs;
+            auto same = [](const MFac& p, const MFac& q) {
+                return p.arr == q.arr && std::memcmp(p.idx, q.idx, 4) == 0;
+            };
+            for (int k = 0; k < mt.cnt[cls]; ++k) {
+                const MTerm& m = mt.terms[mt.off[cls] + k];
+                int nx = 0, nb = 0, nh = 0;
+                MFac xf{}, hf{};
+                for (int f = 0; f < m.nf; ++f) {
+                    const MFac& g = m.f[f];
+                    const int nslot = g.arr < 2 ? 2 : 4;
+                    bool ha = false, hb = false;
+                    for (int r = 0; r < nslot; ++r) {
+                        ha |= g.idx[r] == 2;
+                        hb |= g.idx[r] == 3;
+                    }
+                    if (ha && hb) { ++nh; hf = g; }
+                    else if (ha) { ++nx; xf = g; }
+                    else if (hb) ++nb;
+                }
+                if (nh == 1 && nx == 0 && nb == 0) {
+                    if (std::none_of(hs.begin(), hs.end(), [&](const MFac& q) { return same(q, hf); }))
+                        hs.push_back(hf);
+                } else if (nh == 0 && nx == 1 && nb == 1) {
+                    if (std::none_of(xs.begin(), xs.end(), [&](const MFac& q) { return same(q, xf); }))
+                        xs.push_back(xf);
+                } else {
+                    c->err = "two-determinant table: a term is neither separable nor a joint factor";
+                    return DCSD_ERR_INVALID_ARG;
+                }
+            }
+            g_max_xfac = std::max(g_max_xfac, (int)xs.size());
+            g_max_hfac = std::max(g_max_hfac, (int)hs.size());
+        }
+    return DCSD_OK;
+}
+
 dcsd_status mtables_build(Ctx* c) {
     if (c->device >= 0 && c->device < 64 && g_tables_ready[c->device]) return DCSD_OK;
     static MTerm h_terms[2][kMaxTerms];
@@ -320,6 +374,7 @@ dcsd_status mtables_build(Ctx* c) {
             c->err = "two-determinant table larger than its constant-memory slot";
             return DCSD_ERR_INVALID_ARG;
         }
+        DCSD_TRY(check_separable(c, mt));
         std::memset(h_terms[ref], 0, sizeof(h_terms[ref]));
         std::copy(mt.terms.begin(), mt.terms.end(), h_terms[ref]);
         std::memcpy(h_off[ref], mt.off, sizeof(mt.off));
@@ -403,41 +458,106 @@ __global__ void k_mterm_singles(MArgs a) {
     }
 }
 
-__global__ void k_mterm_doubles(MArgs a) {
+// Doubles: one block per (spin block, i, j).  For the class in which a and
+// b are external virtuals (all but 2V-1 of the block's elements) the block
+// resolves each term's factors once -- with its own i, j substituted -- into
+// (pointer, a-stride, b-stride) descriptors; factors that depend on neither
+// a nor b are folded into the term's coefficient.  Elements with a or b an
+// open orbital use the generic per-element evaluation.
+constexpr int kMaxClassTerms = 64;
+
+struct FacDesc {
+    const double* base;
+    int sa, sb;
+};
+
+__global__ void __launch_bounds__(256) k_mterm_doubles(MArgs a) {
     const long O = a.O, V = a.V;
-    const long nblk = O * O * V * V;
-    const long total = 3 * nblk;
+    const long nb = O * O * V * V;
+    const int slot = blockIdx.x;
+    const int blk = slot / (int)(O * O), i = (slot / (int)O) % (int)O, j = slot % (int)O;
+    const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+    double* Rrow = a.R2 + (long)slot * V * V;
+    bool rowok = occ_ok(a, s1, i) && occ_ok(a, s2, j);
+    if (blk != 2 && i == j) rowok = false;
+    if (!rowok) {
+        for (long e = threadIdx.x; e < V * V; e += blockDim.x) Rrow[e] = 0.0;
+        return;
+    }
+    const bool ai = i == a.occ_act[s1], aj = j == a.occ_act[s2];
+    const int cls_ff = blk * 16 + (ai << 3) + (aj << 2);
+    __shared__ FacDesc fac[kMaxClassTerms][4];
+    __shared__ double coefS[kMaxClassTerms];
+    __shared__ int nfac[kMaxClassTerms];
+    const int toff = c_off[a.ref][cls_ff], nterm = min(c_cnt[a.ref][cls_ff], kMaxClassTerms);
+    for (int k = threadIdx.x; k < nterm; k += blockDim.x) {
+        const MTerm& m = c_terms[a.ref][toff + k];
+        double S = (double)m.sign;
+        int nf = 0;
+        for (int f = 0; f < m.nf; ++f) {
+            const MFac& g = m.f[f];
+            const double* base;
+            long off = 0;
+            int sa = 0, sb = 0;
+            const int nslot = g.arr < 2 ? 2 : 4;
+            const long strides[4] = {g.arr < 2 ? V : O * V * V, g.arr < 2 ? 1 : V * V, V, 1};
+            for (int r = 0; r < nslot; ++r) {
+                const int cd = g.idx[r];
+                const long st = strides[r];
+                if (cd == 2) sa += (int)st;
+                else if (cd == 3) sb += (int)st;
+                else {
+                    const int x = cd == 0 ? i : cd == 1 ? j : cd == 4 ? a.nc : cd == 5 ? a.nc + 1 : cd == 6 ? 0 : 1;
+                    off += (long)x * st;
+                }
+            }
+            if (g.arr < 2) base = a.t1 + (long)g.arr * O * V + off;
+            else if (g.arr < 5) base = a.t2 + (long)(g.arr - 2) * nb + off;
+            else base = a.t2s + (long)(g.arr - 5) * nb + off;
+            if (sa == 0 && sb == 0) {
+                S *= *base;
+            } else {
+                fac[k][nf].base = base;
+                fac[k][nf].sa = sa;
+                fac[k][nf].sb = sb;
+                ++nf;
+            }
+        }
+        coefS[k] = S;
+        nfac[k] = nf;
+    }
+    __syncthreads();
     const double W = *a.W;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-         e += (long)gridDim.x * blockDim.x) {
-        int blk = (int)(e / nblk);
-        long r = e - blk * nblk;
-        int b = (int)(r % V);
-        r /= V;
-        int x = (int)(r % V);
-        r /= V;
-        int j = (int)(r % O);
-        int i = (int)(r / O);
-        int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
-        bool ok = occ_ok(a, s1, i) && occ_ok(a, s2, j) && vir_ok(a, s1, x) && vir_ok(a, s2, b);
-        if (blk != 2 && (i == j || x == b)) ok = false;
-        if (!ok) {
-            a.R2[e] = 0.0;
+    const double* t1a = a.t1;
+    const double* t1b = a.t1 + O * V;
+    const double* c1a = a.c1;
+    const double* c1b = a.c1 + O * V;
+    for (long e = threadIdx.x; e < V * V; e += blockDim.x) {
+        const int x = (int)(e / V), b = (int)(e - (long)x * V);
+        const bool okx = vir_ok(a, s1, x), okb = vir_ok(a, s2, b);
+        if (!okx || !okb || (blk != 2 && x == b)) {
+            Rrow[e] = 0.0;
             continue;
         }
-        bool ai = i == a.occ_act[s1], aj = j == a.occ_act[s2];
-        bool aa = x == a.vir_act[s1], ab = b == a.vir_act[s2];
+        const bool aa = x == a.vir_act[s1], ab = b == a.vir_act[s2];
         if (blk == 2 && ai && aj && aa && ab) {  // the A->B element
-            a.R2[e] = 0.0;
+            Rrow[e] = 0.0;
             continue;
         }
-        int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
-        int q[4] = {i, j, x, b};
-        double c2 = eval_class(a, cls, q);
-        const double* t1a = a.t1;
-        const double* t1b = a.t1 + O * V;
-        const double* c1a = a.c1;
-        const double* c1b = a.c1 + O * V;
+        double c2;
+        if (x >= 2 && b >= 2) {
+            c2 = 0.0;
+            for (int k = 0; k < nterm; ++k) {
+                double prod = coefS[k];
+                const int nf = nfac[k];
+                for (int f = 0; f < nf; ++f) prod *= fac[k][f].base[(long)x * fac[k][f].sa + (long)b * fac[k][f].sb];
+                c2 += prod;
+            }
+        } else {
+            const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
+            const int q[4] = {i, j, x, b};
+            c2 = eval_class(a, cls, q);
+        }
         double tc;
         if (blk == 2) {
             tc = t1a[i * V + x] * c1b[j * V + b] + t1b[j * V + b] * c1a[i * V + x];
@@ -447,7 +567,180 @@ __global__ void k_mterm_doubles(MArgs a) {
             tc = t[i * V + x] * cc[j * V + b] - t[j * V + x] * cc[i * V + b] -
                  t[i * V + b] * cc[j * V + x] + t[j * V + b] * cc[i * V + x];
         }
-        a.R2[e] -= W * (c2 - tc);
+        Rrow[e] -= W * (c2 - tc);
+    }
+}
+
+// Doubles, separable form: one block per (spin block, i, j).  In the class
+// with a and b external the coefficient is
+//   c_ijab = sum_d F_d[a] G_d[b] + sum_m s_m H_m[a][b],
+// where F_d runs over the distinct a-only factors, G_d[b] collects, for each
+// F_d, the coefficient-weighted b-only factors of its terms, and H_m are the
+// distinct joint factors with their summed coefficients.  F and G are built
+// once per block in shared memory, so an element costs (#F + #H) products
+// instead of one product per term.  T is the arithmetic type of the
+// contraction: double for the FP64 residual, float for the tensor-core
+// precisions (whose residual error is far above FP32 rounding).
+constexpr int kMaxXFac = 16, kMaxHFac = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
+    extern __shared__ __align__(16) unsigned char mt_smem[];
+    const long O = a.O, V = a.V;
+    const long nb = O * O * V * V;
+    const int slot = blockIdx.x;
+    const int blk = slot / (int)(O * O), i = (slot / (int)O) % (int)O, j = slot % (int)O;
+    const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+    double* Rrow = a.R2 + (long)slot * V * V;
+    bool rowok = occ_ok(a, s1, i) && occ_ok(a, s2, j);
+    if (blk != 2 && i == j) rowok = false;
+    if (!rowok) {
+        for (long e = threadIdx.x; e < V * V; e += blockDim.x) Rrow[e] = 0.0;
+        return;
+    }
+    const bool ai = i == a.occ_act[s1], aj = j == a.occ_act[s2];
+    const int cls_ff = blk * 16 + (ai << 3) + (aj << 2);
+    __shared__ FacDesc fac[kMaxClassTerms][2];
+    __shared__ double coefS[kMaxClassTerms];
+    __shared__ signed char grp[kMaxClassTerms];  // a-factor group of a separable term, -1 joint
+    __shared__ FacDesc xd[kMaxXFac], hd[kMaxHFac];
+    __shared__ double hc[kMaxHFac];
+    __shared__ int nx_s, nh_s;
+    T* F = (T*)mt_smem;           // [maxx][V]: F_d[a]
+    T* G = F + (long)maxx * V;    // [maxx][V]: G_d[b]
+    const int toff = c_off[a.ref][cls_ff], nterm = min(c_cnt[a.ref][cls_ff], kMaxClassTerms);
+    // (1) resolve each term's factors with this block's i, j; fold the
+    //     factors that hold neither a nor b into the coefficient
+    for (int k = threadIdx.x; k < nterm; k += blockDim.x) {
+        const MTerm& m = c_terms[a.ref][toff + k];
+        double S = (double)m.sign;
+        int nf = 0;
+        for (int f = 0; f < m.nf; ++f) {
+            const MFac& g = m.f[f];
+            long off = 0;
+            int sa = 0, sb = 0;
+            const int nslot = g.arr < 2 ? 2 : 4;
+            const long strides[4] = {g.arr < 2 ? V : O * V * V, g.arr < 2 ? 1 : V * V, V, 1};
+            for (int r = 0; r < nslot; ++r) {
+                const int cd = g.idx[r];
+                const long st = strides[r];
+                if (cd == 2) sa += (int)st;
+                else if (cd == 3) sb += (int)st;
+                else {
+                    const int x = cd == 0 ? i : cd == 1 ? j : cd == 4 ? a.nc : cd == 5 ? a.nc + 1 : cd == 6 ? 0 : 1;
+                    off += (long)x * st;
+                }
+            }
+            const double* base = g.arr < 2 ? a.t1 + (long)g.arr * O * V + off
+                                 : g.arr < 5 ? a.t2 + (long)(g.arr - 2) * nb + off
+                                             : a.t2s + (long)(g.arr - 5) * nb + off;
+            if (sa == 0 && sb == 0) {
+                S *= *base;
+            } else if (nf < 2) {
+                // order: the a-holding factor first
+                if (sb == 0 && nf == 1) {
+                    fac[k][1] = fac[k][0];
+                    fac[k][0] = FacDesc{base, sa, sb};
+                } else {
+                    fac[k][nf] = FacDesc{base, sa, sb};
+                }
+                ++nf;
+            }
+        }
+        coefS[k] = S;
+        grp[k] = (signed char)(nf == 1 ? -1 : 0);
+    }
+    __syncthreads();
+    // (2) group the terms (one thread, fixed order: deterministic sums)
+    if (threadIdx.x == 0) {
+        int nx = 0, nh = 0;
+        for (int k = 0; k < nterm; ++k) {
+            if (grp[k] < 0) {
+                const FacDesc& h = fac[k][0];
+                int m = 0;
+                while (m < nh && !(hd[m].base == h.base && hd[m].sa == h.sa && hd[m].sb == h.sb)) ++m;
+                if (m == nh) {
+                    if (nh == kMaxHFac) { nx = maxx + 1; break; }
+                    hd[nh] = h;
+                    hc[nh] = 0.0;
+                    ++nh;
+                }
+                hc[m] += coefS[k];
+            } else {
+                const FacDesc& x = fac[k][0];
+                int d = 0;
+                while (d < nx && !(xd[d].base == x.base && xd[d].sa == x.sa)) ++d;
+                if (d == nx) {
+                    if (nx == maxx) { nx = maxx + 1; break; }
+                    xd[nx++] = x;
+                }
+                grp[k] = (signed char)d;
+            }
+        }
+        nx_s = nx;
+        nh_s = nh;
+    }
+    __syncthreads();
+    // the host bounds both counts; a table outside them takes the per-term
+    // evaluation for every element
+    const bool generic = nx_s > maxx;
+    const int nx = generic ? 0 : nx_s, nh = generic ? 0 : nh_s;
+    // (3) F_d[a] and G_d[b]
+    for (int b = threadIdx.x; b < V && !generic; b += blockDim.x) {
+        for (int d = 0; d < nx; ++d) {
+            F[(long)d * V + b] = (T)xd[d].base[(long)b * xd[d].sa];
+            G[(long)d * V + b] = (T)0;
+        }
+        for (int k = 0; k < nterm; ++k)
+            if (grp[k] >= 0)
+                G[(long)grp[k] * V + b] += (T)(coefS[k] * fac[k][1].base[(long)b * fac[k][1].sb]);
+    }
+    __syncthreads();
+    const double W = *a.W;
+    const T Wt = (T)W;
+    const double* t1a = a.t1;
+    const double* t1b = a.t1 + O * V;
+    const double* c1a = a.c1;
+    const double* c1b = a.c1 + O * V;
+    const double* tA = blk == 1 ? t1b : t1a;  // spin of a (s1)
+    const double* cA = blk == 1 ? c1b : c1a;
+    const double* tB = blk == 0 ? t1a : t1b;  // spin of b (s2)
+    const double* cB = blk == 0 ? c1a : c1b;
+    for (int x = 0; x < V; ++x) {
+        const bool okx = vir_ok(a, s1, x);
+        const bool aa = x == a.vir_act[s1];
+        // row-invariant parts of the antisymmetrised t1 c1 product
+        const T tia = (T)tA[i * V + x], cia = (T)cA[i * V + x];
+        const T tja = (T)tA[j * V + x], cja = (T)cA[j * V + x];
+        for (int b = threadIdx.x; b < V; b += blockDim.x) {
+            const long e = (long)x * V + b;
+            const bool okb = vir_ok(a, s2, b);
+            if (!okx || !okb || (blk != 2 && x == b)) {
+                Rrow[e] = 0.0;
+                continue;
+            }
+            const bool ab = b == a.vir_act[s2];
+            if (blk == 2 && ai && aj && aa && ab) {  // the A->B element
+                Rrow[e] = 0.0;
+                continue;
+            }
+            T tc;
+            if (blk == 2) tc = tia * (T)c1b[j * V + b] + (T)t1b[j * V + b] * cia;
+            else
+                tc = tia * (T)cB[j * V + b] - tja * (T)cB[i * V + b] - (T)tB[i * V + b] * cja +
+                     (T)tB[j * V + b] * cia;
+            if (x >= 2 && b >= 2 && !generic) {
+                T c2 = (T)0;
+                for (int d = 0; d < nx; ++d) c2 += F[(long)d * V + x] * G[(long)d * V + b];
+                for (int m = 0; m < nh; ++m)
+                    c2 += (T)hc[m] * (T)hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb];
+                Rrow[e] -= (double)(Wt * (c2 - tc));
+            } else {
+                const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
+                const int q[4] = {i, j, x, b};
+                Rrow[e] -= W * (eval_class(a, cls, q) - (double)tc);
+            }
+        }
     }
 }
 
@@ -473,7 +766,7 @@ __global__ void k_swap_vir(long nmat, int V, const double* t2, double* t2s) {
     }
 }
 
-dcsd_status apply_mterms(Ctx* c, int ref) {
+dcsd_status apply_mterms(Ctx* c, int ref, bool fp32) {
     MArgs a;
     a.O = c->O; a.V = c->V; a.nc = c->nc; a.ref = ref;
     Frame f = frame_of(c, ref);
@@ -483,15 +776,30 @@ dcsd_status apply_mterms(Ctx* c, int ref) {
     {
         const long nmat = 3l * c->O * c->O, tv = (c->V + 31) / 32;
         const long blocks = std::min<long>(nmat * tv * tv, (long)std::max(c->num_sms, 1) * 16);
+        trace_begin(c, "swap_vir");
         k_swap_vir<<<(unsigned)std::max<long>(1, blocks), 256, 0, c->stream>>>(nmat, c->V, c->t2, c->t2s);
+        trace_end(c);
         DCSD_TRY(launch_check(c, "swap_vir"));
     }
     long n1 = 2l * c->O * c->V;
     k_mterm_singles<<<(unsigned)std::max<long>(1, (n1 + 255) / 256), 256, 0, c->stream>>>(a);
     DCSD_TRY(launch_check(c, "mterm_singles"));
-    long n2 = 3l * c->O * c->O * c->V * c->V;
-    long g = std::min<long>((n2 + 255) / 256, (long)std::max(c->num_sms, 1) * 32);
-    k_mterm_doubles<<<(unsigned)g, 256, 0, c->stream>>>(a);
+    const int maxx = std::max(g_max_xfac, 1);
+    const size_t smem = 2ul * maxx * c->V * (fp32 ? sizeof(float) : sizeof(double));
+    const unsigned grid = (unsigned)(3l * c->O * c->O);
+    trace_begin(c, fp32 ? "mterm_doubles_sep32" : "mterm_doubles_sep64");
+    if (g_max_xfac > kMaxXFac || g_max_hfac > kMaxHFac || smem > 160 * 1024) {
+        k_mterm_doubles<<<grid, 256, 0, c->stream>>>(a);  // per-term form (large V)
+    } else if (fp32) {
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_mterm_doubles_sep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        k_mterm_doubles_sep<float><<<grid, 256, smem, c->stream>>>(a, maxx);
+    } else {
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_mterm_doubles_sep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        k_mterm_doubles_sep<double><<<grid, 256, smem, c->stream>>>(a, maxx);
+    }
+    trace_end(c);
     return launch_check(c, "mterm_doubles");
 }
 

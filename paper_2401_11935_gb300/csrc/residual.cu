@@ -269,11 +269,11 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
                     }
                 }
                 if (sg == sp) {
-                    TV R = blk(R2, sg);
-                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {0, 2, 1, 3}), 1.0, R));
-                    DCSD_TRY(axpy_view(c, -1.0, perm(Xacc, {2, 0, 1, 3}), 1.0, R));
-                    DCSD_TRY(axpy_view(c, -1.0, perm(Xacc, {0, 2, 3, 1}), 1.0, R));
-                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {2, 0, 3, 1}), 1.0, R));
+                    // R += P(ij)P(ab) X  (one pass)
+                    const TV views[4] = {perm(Xacc, {0, 2, 1, 3}), perm(Xacc, {2, 0, 1, 3}),
+                                         perm(Xacc, {0, 2, 3, 1}), perm(Xacc, {2, 0, 3, 1})};
+                    const double al[4] = {1.0, -1.0, -1.0, 1.0};
+                    DCSD_TRY(axpy4(c, 4, al, views, blk(R2, sg)));
                 } else if (sg == 0) {
                     DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {0, 2, 1, 3}), 1.0, blk(R2, 2)));
                 } else {
@@ -333,7 +333,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         DCSD_CUDA(c, cudaMemcpyAsync(c->scal, c->R2 + e, sizeof(double), cudaMemcpyDeviceToDevice,
                                      c->stream));
     }
-    DCSD_TRY(apply_mterms(c, ref));
+    DCSD_TRY(apply_mterms(c, ref, prec != DCSD_PREC_FP64));
     return DCSD_OK;
 }
 

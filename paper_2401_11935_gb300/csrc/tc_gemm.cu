@@ -179,13 +179,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kStageBytesMode2 = 4 * 32 * 64 * 2;  // epilogue staging, 4 warps x 2 halves x 32 rows x 64 B
+constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, each on half of the columns
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
+constexpr int kStageBytesMode2 = kEpiWarps * 32 * 64 * 2;  // epilogue staging, per warp 2 halves x 32 rows x 64 B
 
 // Persistent tcgen05 GEMM: one CTA per SM walks the output tiles (m fastest);
 // two TMEM accumulators of BN columns let the epilogue of one tile overlap
 // the MMAs of the next.
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
               int nkt, int tilesM, int tilesN, int* err) {
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);
+            mbar_init(&acce[b], kEpiWarps);
         }
         *issued = 0;
         *consumed = 0;
@@ -284,8 +286,10 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // epilogue warps 2..5 -> TMEM lane quarter (warp % 4)
+        // epilogue warps 2..9 -> TMEM lane quarter (warp % 4); warps 2..5 take
+        // the first half of the tile's columns, warps 6..9 the second
         const int q = warp & 3;
+        const int ch0 = ((warp - 2) >> 2) * (BN / 64), ch1 = ch0 + BN / 64;
         int j = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
             const int buf = j & 1, u = j >> 1;
@@ -301,13 +305,13 @@ __global__ void __launch_bounds__(192, 1)
                 // lane = row; BF16 conversion staged through shared memory, then
                 // each row's 64 contiguous bytes go out as four 16-byte vectors,
                 // 8 rows per warp instruction
-                uint4* stage = (uint4*)(staging + q * 32 * 64 * 2);
+                uint4* stage = (uint4*)(staging + (warp - 2) * 32 * 64 * 2);
                 const long m = (long)m0 + 32 * q + lane;
                 const long r_of = m / epi.V, c_of = m - r_of * epi.V;
                 const long rowbase = r_of * epi.Vb * epi.rowlen + c_of * epi.Vp;
                 const float alpha = (float)epi.alpha;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {
+                for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t rr[32];
                     tmem_ld32(tbase + (uint32_t)(ch * 32), rr);
                     const long nst = (long)n0 + ch * 32;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(192, 1)
                 const long ij = m - (long)sblk * epi.OO;
                 double* Rb = epi.C + (long)(sblk < 2 ? sblk : 2) * epi.OO * epi.VV + ij * epi.VV;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {
+                for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)(ch * 32), r);
                     if (!rowok) continue;
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(192, 1)
                 const long roff = rowok ? decomp1(m, epi.nm, epi.m_size, epi.m_s) : 0;
                 const float alpha = (float)epi.alpha;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {
+                for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)(ch * 32), r);
                     if (!rowok) continue;
@@ -472,43 +476,79 @@ struct PackArgs {
     long rvalid, kvalid;  // innermost row / k mode indices >= these read as 0
 };
 
+// offset of a linear index over up to kMaxMode modes (last mode fastest);
+// indices and mode sizes are below 2^31, so the divisions are 32-bit
+__device__ __forceinline__ long decomp1_u32(unsigned idx, int nmode, const long* size, const long* s) {
+    long o = 0;
+#pragma unroll
+    for (int j = kMaxMode - 1; j >= 0; --j) {
+        if (j < nmode) {
+            const unsigned sz = (unsigned)size[j];
+            const unsigned q = idx / sz;
+            o += (long)(idx - q * sz) * s[j];
+            idx = q;
+        }
+    }
+    return o;
+}
+
+// 64 rows x 64 k per tile: coalesced FP64 reads (along whichever of row or k
+// is contiguous in the source), conversion to FP32 in shared memory, then
+// 16-byte stores of 8 BF16 values per segment.
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
-    __shared__ double tile[32][65];
-    __shared__ long roff[32], koff[64];
-    const long ntr = (a.rows + 31) / 32, ntk = (a.Kp + 63) / 64;
+    __shared__ float tile[64][65];
+    __shared__ long roff[64], koff[64];
+    const long ntr = (a.rows + 63) / 64, ntk = (a.Kp + 63) / 64;
+    const long ldd = (long)a.nseg * a.Kp;
     for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
-        const long r0 = (t / ntk) * 32, k0 = (t % ntk) * 64;
+        const long r0 = (t / ntk) * 64, k0 = (t % ntk) * 64;
         // source offsets of the tile's rows and columns (-1: reads as zero)
-        if (threadIdx.x < 32) {
+        if (threadIdx.x < 64) {
             const long r = r0 + threadIdx.x;
             long o = -1;
-            if (r < a.rows && (a.nr == 0 || (r % a.r_size[a.nr - 1]) < a.rvalid))
-                o = decomp1(r, a.nr, a.r_size, a.r_s);
+            if (r < a.rows) {
+                const unsigned ru = (unsigned)r;
+                if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
+                    o = decomp1_u32(ru, a.nr, a.r_size, a.r_s);
+            }
             roff[threadIdx.x] = o;
-        } else if (threadIdx.x < 96) {
-            const int kk = threadIdx.x - 32;
+        } else if (threadIdx.x < 128) {
+            const int kk = threadIdx.x - 64;
             const long k = k0 + kk;
             long o = -1;
-            if (k < a.K && (a.nk == 0 || (k % a.k_size[a.nk - 1]) < a.kvalid))
-                o = decomp1(k, a.nk, a.k_size, a.k_s);
+            if (k < a.K) {
+                const unsigned ku = (unsigned)k;
+                if (a.nk == 0 || (long)(ku % (unsigned)a.k_size[a.nk - 1]) < a.kvalid)
+                    o = decomp1_u32(ku, a.nk, a.k_size, a.k_s);
+            }
             koff[kk] = o;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < 64 * 64; e += 256) {
             int rr, kk;
             if (a.kfast) { kk = e & 63; rr = e >> 6; }
-            else { rr = e & 31; kk = e >> 5; }
+            else { rr = e & 63; kk = e >> 6; }
             const long ro = roff[rr], ko = koff[kk];
-            tile[rr][kk] = (ro >= 0 && ko >= 0) ? a.src[ro + ko] : 0.0;
+            tile[rr][kk] = (ro >= 0 && ko >= 0) ? (float)a.src[ro + ko] : 0.0f;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-            const int kk = e & 63, rr = e >> 6;
-            const long r = r0 + rr, k = k0 + kk;
-            if (r < a.rows && k < a.Kp) {
-                const float v = (float)tile[rr][kk];
-                __nv_bfloat16* d = a.dst + r * (a.nseg * a.Kp) + k;
-                for (int s = 0; s < a.nseg; ++s) d[s * a.Kp] = split_part(v, a.pat[s]);
+        // 64 rows x 8 groups of 8 k: 8 consecutive threads cover one row
+        for (int it = threadIdx.x; it < 64 * 8; it += 256) {
+            const int g = it & 7, rr = it >> 3;
+            const long r = r0 + rr;
+            if (r >= a.rows) continue;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = tile[rr][g * 8 + q];
+            __nv_bfloat16* d = a.dst + r * ldd + k0 + g * 8;
+            for (int sg = 0; sg < a.nseg; ++sg) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = (uint32_t)__bfloat16_as_ushort(split_part(v[2 * q], a.pat[sg])) |
+                           ((uint32_t)__bfloat16_as_ushort(split_part(v[2 * q + 1], a.pat[sg])) << 16);
+                *(uint4*)(d + (long)sg * a.Kp) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         __syncthreads();
@@ -611,7 +651,11 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
         a.k_s[i] = i < nk ? ks[i] : 0;
     }
     a.kfast = (nk > 0 && ks[nk - 1] == 1) ? 1 : 0;
-    long tiles = ((rows + 31) / 32) * ((Kp + 63) / 64);
+    if (Kp % 64 != 0 || rows >= (1l << 31) || Kp >= (1l << 31)) {
+        c->err = "pack: K padding must be a multiple of 64 and sizes below 2^31";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    long tiles = ((rows + 63) / 64) * (Kp / 64);
     unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, (long)c->num_sms * 8));
     prof_begin(c, DCSD_PROF_PACK);
     if (c->trace)
@@ -654,9 +698,9 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
         trace_begin(c, std::string(c->ladder_phase ? "tc-ladder " : "tc ") + c->cur_spec + " mode=" + std::to_string(epi.mode) +
                            " M=" + std::to_string(M) + " N=" + std::to_string(N) + " Kt=" + std::to_string(Ktot));
     if (BN == 256)
-        k_tc_gemm<256><<<grid, 192, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
     else
-        k_tc_gemm<128><<<grid, 192, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
     trace_end(c);
     prof_end(c, cls);
     return launch_check(c, "tc_gemm");
@@ -705,11 +749,25 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
     split_patterns(nsplit, nseg, pa, pb);
     const long Kp = round_up(p.K, TC_BK);
     const long Kt = nseg * Kp;
+    // Row order within M (and N) is free: the packed operand and the
+    // epilogue only have to agree.  Order each side's modes by decreasing
+    // stride in C, so that its fastest mode is the one closest to C's
+    // contiguous axis.
+    auto order_modes = [](int nmode, long* size, long* s_op, long* s_c) {
+        for (int a = 1; a < nmode; ++a)
+            for (int b = a; b > 0 && std::labs(s_c[b - 1]) < std::labs(s_c[b]); --b) {
+                std::swap(size[b - 1], size[b]);
+                std::swap(s_op[b - 1], s_op[b]);
+                std::swap(s_c[b - 1], s_c[b]);
+            }
+    };
+    order_modes(p.nm, p.m_size, p.m_sa, p.m_sc);
+    order_modes(p.nn, p.n_size, p.n_sb, p.n_sc);
     // The epilogue maps TMEM lanes (tile rows) to consecutive m: put on the
-    // m side whichever operand indexes the contiguous axis of C.
-    const bool m_contig = p.nm > 0 && p.m_sc[p.nm - 1] == 1;
-    const bool n_contig = p.nn > 0 && p.n_sc[p.nn - 1] == 1;
-    if (!m_contig && n_contig) {
+    // m side the operand whose fastest mode has the smaller stride in C.
+    const long m_fast = p.nm > 0 ? std::labs(p.m_sc[p.nm - 1]) : (1l << 62);
+    const long n_fast = p.nn > 0 ? std::labs(p.n_sc[p.nn - 1]) : (1l << 62);
+    if (n_fast < m_fast) {
         GemmPlan q = p;
         q.nm = p.nn; q.nn = p.nm; q.M = p.N; q.N = p.M;
         for (int i = 0; i < kMaxMode; ++i) {
