@@ -201,6 +201,18 @@ typedef enum {
 dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
                          long long* launches);
 
+/* dcsd_selftest_conversions -- checks, on the current device, the FP64 <->
+ * FP32 conversions that the tensor-core precision modes perform on the
+ * integer units (IEEE 754 binary64/binary32, round to nearest even) against
+ * the hardware conversions: every binary32 value to binary64, and 2^28
+ * binary64 patterns covering every exponent with exact ties, near-ties and
+ * random fractions to binary32.  NaN results compare equal to any NaN.  Not
+ * part of the paper's method: a check of this library's arithmetic.
+ *   stream     : cudaStream_t the kernels run on (synchronised before return).
+ *   mismatches : host pointer receiving the number of differing results.
+ * Errors: INVALID_ARG (NULL mismatches), NO_DEVICE, OOM, CUDA. */
+dcsd_status dcsd_selftest_conversions(void* stream, long long* mismatches);
+
 /* dcsd_energy_noalloc -- Delta E_A (the first term of Eq. 2, as returned by
  * dcsd_energy) for callers that cannot allocate device memory: code that is
  * capturing a CUDA graph, that hands all device memory to its own pool

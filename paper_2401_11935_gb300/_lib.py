@@ -22,7 +22,7 @@ PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
-           "dcsd_energy_noalloc"]
+           "dcsd_energy_noalloc", "dcsd_selftest_conversions"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -75,6 +75,8 @@ def load():
     lib.dcsd_profile.restype = C.c_int
     lib.dcsd_energy_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10
     lib.dcsd_energy_noalloc.restype = C.c_int
+    lib.dcsd_selftest_conversions.argtypes = [P, C.POINTER(C.c_longlong)]
+    lib.dcsd_selftest_conversions.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -155,3 +157,13 @@ def dcsd_energy_noalloc(n_c, n_v, naux, ref, fock_a, fock_b, B, T, dEA, stream):
     st = load().dcsd_energy_noalloc(n_c, n_v, naux, ref, fock_a, fock_b, B, *T, dEA, stream)
     if st != DCSD_OK:
         raise DcsdError(st, "dcsd_energy_noalloc failed")
+
+
+def dcsd_selftest_conversions(stream=None):
+    """Number of mismatches between the library's integer-unit FP64<->FP32
+    conversions and the hardware conversions on the current device."""
+    n = C.c_longlong(-1)
+    st = load().dcsd_selftest_conversions(stream, C.byref(n))
+    if st != 0:
+        raise DcsdError(st, "dcsd_selftest_conversions failed")
+    return n.value

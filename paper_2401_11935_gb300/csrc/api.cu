@@ -79,14 +79,24 @@ __global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V
         } else {
             const long base = 2l * O * V + (row - nrow1) * V * V;
             const double dij = f1[(long)i * n + i] + f2[(long)j * n + j];
-            for (int x = 0; x < V; ++x) {
-                const double Da = d1[x * d1s] - dij;
-                const long rb = base + (long)x * V;
-                for (int b = threadIdx.x; b < V; b += blockDim.x) {
-                    const double r = R[rb + b];
-                    const double st = r != 0.0 ? -r * recip_nr(Da + d2[b * d2s]) : 0.0;
-                    step[rb + b] = st;
-                    tnew[rb + b] = t[rb + b] + st;
+            const unsigned VV = (unsigned)V * (unsigned)V, bs = blockDim.x;
+            // four elements per thread and pass (eight loads in flight)
+            for (unsigned e0 = threadIdx.x; e0 < VV; e0 += 4 * bs) {
+                double r[4], tt[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned e = e0 + q * bs;
+                    r[q] = e < VV ? R[base + e] : 0.0;
+                    tt[q] = e < VV ? t[base + e] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned e = e0 + q * bs;
+                    if (e >= VV) break;
+                    const unsigned x = e / (unsigned)V, b = e - x * (unsigned)V;
+                    const double st = r[q] != 0.0 ? -r[q] * recip_nr(d1[x * d1s] - dij + d2[b * d2s]) : 0.0;
+                    step[base + e] = st;
+                    tnew[base + e] = tt[q] + st;
                 }
             }
         }
@@ -126,16 +136,27 @@ struct LinComb {
     int m;
 };
 
-__global__ void k_lincomb(LinComb lc, long n, double* out) {
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < lc.m; ++k) s += lc.coef[k] * lc.v[k][e];
-        out[e] = s;
+__global__ void __launch_bounds__(256) k_lincomb(LinComb lc, long n, double* out) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    for (; e + stride < n; e += 2 * stride) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = 0; k < lc.m; ++k) {
+            s0 += lc.coef[k] * lc.v[k][e];
+            s1 += lc.coef[k] * lc.v[k][e + stride];
+        }
+        out[e] = s0;
+        out[e + stride] = s1;
+    }
+    if (e < n) {
+        double s0 = 0.0;
+        for (int k = 0; k < lc.m; ++k) s0 += lc.coef[k] * lc.v[k][e];
+        out[e] = s0;
     }
 }
 
 static unsigned grid_n(Ctx* c, long n) {
-    long g = (n + 255) / 256, cap = (long)std::max(c->num_sms, 1) * 16;
+    long g = (n + 255) / 256, cap = (long)std::max(c->num_sms, 1) * 8;
     return (unsigned)std::max<long>(1, std::min(g, cap));
 }
 
@@ -181,6 +202,8 @@ void free_ctx(Ctx* c) {
     }
     c->t2 = nullptr;
     c->R2 = nullptr;
+    if (c->r2f) cudaFree(c->r2f);
+    c->r2f = nullptr;
     if (c->hostbuf) cudaFreeHost(c->hostbuf);
     c->hostbuf = nullptr;
     for (int k = 0; k < 8; ++k) {
@@ -264,7 +287,8 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
     c->stream = (cudaStream_t)stream;
     {
         const char* tr = getenv("DCSD_TRACE");
-        c->trace = tr && tr[0] == '1';
+        c->trace = tr && (tr[0] == '1' || tr[0] == '2');
+        c->trace_seq = tr && tr[0] == '2';
         const char* vb = getenv("DCSD_VERBOSE");
         c->verbose = vb && vb[0] == '1';
     }

@@ -56,7 +56,7 @@ struct MTables;   // two-determinant coupling tables (mterm.cu)
 struct TcEngine;  // tensor-core contraction engine (tc_gemm.cu)
 
 // reduction scratch (Ctx::red), in doubles
-constexpr int kRedDoubles = 16384;
+constexpr int kRedDoubles = 32768;
 
 struct Ctx {
     int nc = 0, nv = 0, X = 0;
@@ -101,6 +101,12 @@ struct Ctx {
     size_t splitk_elems = 0;
     double* scal = nullptr;       // device scalars: [0]=W [1]=dEA [2..] misc
     double* c1 = nullptr;         // [2][O][V] two-determinant coefficients
+    // tensor-core modes: FP32 accumulator shadowing R2.  While r2f_on, the
+    // tensor-core GEMMs that accumulate into R2 (beta = 1) add into r2f
+    // instead (same element offsets); the residual adds it to R2 before W is
+    // read.
+    float* r2f = nullptr;
+    bool r2f_on = false;
     double* hostbuf = nullptr;    // pinned host staging for scalars
     int ladder_chunk = 8;         // virtual rows per V build chunk (FP64)
 
@@ -114,6 +120,8 @@ struct Ctx {
     int ladder_phase = 0;         // set while the ladder GEMMs run (profile class)
     // DCSD_TRACE=1: per-call device time by label, summarised to stderr on destroy
     bool trace = false;
+    bool trace_seq = false;  // also list every tensor-core GEMM launch in order
+    int tc_seq = 0;          // tensor-core GEMM launches so far
     bool verbose = false;         // DCSD_VERBOSE=1: per-iteration solver log on stderr
     std::string cur_spec;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
@@ -123,6 +131,41 @@ struct Ctx {
     double* diis_e = nullptr;     // [nd][len]
     int diis_cap = 0;
 };
+
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversion on the integer units.  On this GPU a hardware
+// F64<->F32 conversion issues on the FP64 pipe, which runs at about 1/30 of
+// the FP32 rate; these do the same conversion with 32-bit integer
+// operations, from the IEEE 754 binary32/binary64 encodings (sign, biased
+// exponent, fraction; biases 127 and 1023).  Results whose binary32 form is
+// subnormal take the hardware conversion (rare: |x| < 2^-126).
+// ---------------------------------------------------------------------------
+// binary32 -> binary64, exact
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu, sgn = u & 0x80000000u;
+    if (e == 0u) return m == 0u ? __hiloint2double((int)sgn, 0) : (double)x;
+    const unsigned ed = e == 0xFFu ? 0x7FFu : e + 896u;  // 1023 - 127
+    return __hiloint2double((int)(sgn | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// binary64 -> binary32, round to nearest, ties to even
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    if (e == 0x7FF) {  // infinity or NaN
+        const bool nan = ((hi & 0xFFFFFu) | lo) != 0u;
+        return __uint_as_float(sgn | 0x7F800000u | (nan ? 0x400000u : 0u));
+    }
+    const int ef = e - 896;
+    if (ef >= 0xFF) return __uint_as_float(sgn | 0x7F800000u);  // overflow
+    if (ef <= 0) return e == 0 ? __uint_as_float(sgn) : (float)x;  // zero / subnormal result
+    const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rem = lo & 0x1FFFFFFFu;
+    unsigned bits = sgn | ((unsigned)ef << 23) | m23;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ++bits;  // carry may reach infinity
+    return __uint_as_float(bits);
+}
 
 // error helpers
 #define DCSD_CUDA(ctx, call)                                                  \
@@ -144,6 +187,10 @@ struct Ctx {
 // kernels (launchers return DCSD_OK or set ctx->err)
 // ---------------------------------------------------------------------------
 dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A,
+                     const TV& B, double beta, const TV& C);
+// same contraction with FP32 products (FP64 accumulation across k-tiles);
+// rows or columns of length 1 still take the FP64 matrix-vector kernel
+dcsd_status einsum32(Ctx* c, const char* spec, double alpha, const TV& A,
                      const TV& B, double beta, const TV& C);
 // C (+)= alpha * A elementwise over identical index sets (4D max), any strides
 dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& C);
@@ -168,6 +215,8 @@ dcsd_status check_finite(Ctx* c, const double* p, size_t n, double* flag);
 // two-determinant layer
 dcsd_status mtables_build(Ctx* c);
 void mtables_free(Ctx* c);
+// R2 += r2f (FP32 accumulator of the tensor-core GEMMs)
+dcsd_status merge_r2f(Ctx* c);
 // coupling terms; fp32 = evaluate the doubles coefficient products in FP32
 dcsd_status apply_mterms(Ctx* c, int ref, bool fp32);
 

@@ -252,9 +252,14 @@ __device__ __forceinline__ void decomp2(long idx, int nmode, const long* size, c
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
-    __shared__ double As[GBK][GBM + 1];
-    __shared__ double Bs[GBK][GBN + 1];
+// T = double: FP64 products and accumulation.  T = float: FP32 products of
+// the FP64 inputs (each loaded element is converted once and reused across
+// the 64-wide tile), summed in FP32 over one k-tile of GBK and accumulated in
+// FP64 across k-tiles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_t(GemmArgs g) {
+    __shared__ T As[GBK][GBM + 1];
+    __shared__ T Bs[GBK][GBN + 1];
     __shared__ long rA[GBM], rC[GBM], cB[GBN], cC[GBN];
     __shared__ long kA[GBK], kB[GBK];
     const GemmPlan& p = g.p;
@@ -302,19 +307,24 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
                 if (g.a_kfast) { kk = e % GBK; mm = e / GBK; }
                 else { mm = e % GBM; kk = e / GBM; }
                 long ra = rA[mm], ka = kA[kk];
-                As[kk][mm] = (ra >= 0 && ka >= 0) ? g.A[oA + ra + ka] : 0.0;
+                As[kk][mm] = (ra >= 0 && ka >= 0) ? (T)g.A[oA + ra + ka] : (T)0;
             }
             for (int e = tid; e < GBN * GBK; e += 256) {
                 int nn, kk;
                 if (g.b_kfast) { kk = e % GBK; nn = e / GBK; }
                 else { nn = e % GBN; kk = e / GBN; }
                 long cb = cB[nn], kb = kB[kk];
-                Bs[kk][nn] = (cb >= 0 && kb >= 0) ? g.B[oB + cb + kb] : 0.0;
+                Bs[kk][nn] = (cb >= 0 && kb >= 0) ? (T)g.B[oB + cb + kb] : (T)0;
             }
             __syncthreads();
+            T part[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) part[i][j] = sizeof(T) == 8 ? (T)acc[i][j] : (T)0;
 #pragma unroll
             for (int kk = 0; kk < GBK; ++kk) {
-                double a[4], b[4];
+                T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -322,8 +332,13 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs g) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < 4; ++j) part[i][j] = fma(a[i], b[j], part[i][j]);
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = sizeof(T) == 8 ? (double)part[i][j] : acc[i][j] + (double)part[i][j];
         }
         if (g.nsplit > 1) {
 #pragma unroll
@@ -402,8 +417,21 @@ __global__ void __launch_bounds__(256) k_gemv64(GemmArgs g, int vec_is_b) {
     }
 }
 
+static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
+                               double beta, const TV& C, bool fp32);
+
 dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
                      double beta, const TV& C) {
+    return einsum_simt(c, spec, alpha, A, B, beta, C, false);
+}
+
+dcsd_status einsum32(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
+                     double beta, const TV& C) {
+    return einsum_simt(c, spec, alpha, A, B, beta, C, true);
+}
+
+static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
+                               double beta, const TV& C, bool fp32) {
     GemmArgs g;
     std::string err;
     if (!plan_einsum(spec, A, B, C, g.p, err)) {
@@ -450,10 +478,11 @@ dcsd_status einsum64(Ctx* c, const char* spec, double alpha, const TV& A, const 
               (unsigned)(g.nsplit > 1 ? g.nsplit : std::min<long>(g.p.NB, 65535)));
     prof_begin(c, DCSD_PROF_FP64);
     if (c->trace)
-        trace_begin(c, std::string("fp64 ") + spec + " M=" + std::to_string(g.p.M) + " N=" +
+        trace_begin(c, std::string(fp32 ? "fp32 " : "fp64 ") + spec + " M=" + std::to_string(g.p.M) + " N=" +
                            std::to_string(g.p.N) + " K=" + std::to_string(g.p.K) + " B=" +
                            std::to_string(g.p.NB) + " split=" + std::to_string(g.nsplit));
-    k_gemm64<<<grid, 256, 0, c->stream>>>(g);
+    if (fp32) k_gemm_t<float><<<grid, 256, 0, c->stream>>>(g);
+    else k_gemm_t<double><<<grid, 256, 0, c->stream>>>(g);
     if (g.nsplit > 1) {
         long tot = g.p.M * g.p.N;
         k_splitk_reduce<<<grid_for(c, tot), 256, 0, c->stream>>>(g.p, g.nsplit, g.ws, g.C, alpha, beta);
@@ -476,38 +505,67 @@ struct EwArgs {
     double alpha, beta;
 };
 
+// linear index -> (offset in A, offset in C); I = unsigned when the element
+// count fits 32 bits (cheaper divisions)
+template <typename I>
+__device__ __forceinline__ void ew_offsets(const EwArgs& a, I idx, long& oa, long& oc) {
+    oa = 0;
+    oc = 0;
+    for (int j = a.rank - 1; j > 0; --j) {
+        const I sz = (I)a.size[j];
+        const I q = idx / sz, r = idx - q * sz;
+        oa += (long)r * a.sa[j];
+        oc += (long)r * a.sc[j];
+        idx = q;
+    }
+    oa += (long)idx * a.sa[0];
+    oc += (long)idx * a.sc[0];
+}
+
+template <typename I>
 __global__ void k_axpy_view(EwArgs a) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.total;
          e += (long)gridDim.x * blockDim.x) {
-        long idx = e, oa = 0, oc = 0;
-        for (int j = a.rank - 1; j >= 0; --j) {
-            long q = idx / a.size[j], r = idx - q * a.size[j];
-            oa += r * a.sa[j];
-            oc += r * a.sc[j];
-            idx = q;
-        }
+        long oa, oc;
+        ew_offsets<I>(a, (I)e, oa, oc);
         double v = a.alpha * a.A[oa];
         if (a.beta != 0.0) v += a.beta * a.C[oc];
         a.C[oc] = v;
     }
 }
 
+// Shapes and strides of A and C, with size-1 modes dropped and adjacent
+// modes merged where both views are contiguous across them.
 static bool ew_setup(Ctx* c, const TV& A, const TV& C, EwArgs& a) {
     if (A.rank != C.rank || A.rank > 6) {
         c->err = "elementwise view rank mismatch";
         return false;
     }
-    a.rank = A.rank;
+    a.rank = 0;
     a.total = 1;
     for (int i = 0; i < A.rank; ++i) {
         if (A.size[i] != C.size[i]) {
             c->err = "elementwise view size mismatch";
             return false;
         }
-        a.size[i] = A.size[i];
-        a.sa[i] = A.stride[i];
-        a.sc[i] = C.stride[i];
         a.total *= A.size[i];
+        if (A.size[i] == 1) continue;
+        if (a.rank > 0 && a.sa[a.rank - 1] == A.stride[i] * A.size[i] &&
+            a.sc[a.rank - 1] == C.stride[i] * A.size[i]) {
+            a.size[a.rank - 1] *= A.size[i];
+            a.sa[a.rank - 1] = A.stride[i];
+            a.sc[a.rank - 1] = C.stride[i];
+            continue;
+        }
+        a.size[a.rank] = A.size[i];
+        a.sa[a.rank] = A.stride[i];
+        a.sc[a.rank] = C.stride[i];
+        ++a.rank;
+    }
+    if (a.rank == 0) {
+        a.rank = 1;
+        a.size[0] = 1;
+        a.sa[0] = a.sc[0] = 0;
     }
     return true;
 }
@@ -527,7 +585,8 @@ dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& 
     a.alpha = alpha;
     a.beta = beta;
     if (c->trace) trace_begin(c, "axpy rank=" + std::to_string(a.rank) + " n=" + std::to_string(a.total));
-    k_axpy_view<<<grid_for(c, a.total), 256, 0, c->stream>>>(a);
+    if (a.total < (1l << 32)) k_axpy_view<unsigned><<<grid_for(c, a.total), 256, 0, c->stream>>>(a);
+    else k_axpy_view<unsigned long><<<grid_for(c, a.total), 256, 0, c->stream>>>(a);
     trace_end(c);
     return launch_check(c, "axpy_view");
 }
@@ -596,21 +655,30 @@ struct MultiDotArgs {
     double* partial;  // [m][gridDim.x]
 };
 
+template <int MM>
 __global__ void __launch_bounds__(256) k_multidot_partial(MultiDotArgs a) {
-    __shared__ double sh[8][16];
-    double acc[16];
+    __shared__ double sh[8][MM];
+    double acc[MM];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.n; e += (long)gridDim.x * blockDim.x) {
-        const double xv = a.x[e];
+    for (int k = 0; k < MM; ++k) acc[k] = 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    // two elements per thread and pass: 2 (m + 1) independent loads in flight
+    for (; e + stride < a.n; e += 2 * stride) {
+        const double x0 = a.x[e], x1 = a.x[e + stride];
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < a.m) acc[k] = fma(xv, a.y[k][e], acc[k]);
+        for (int k = 0; k < MM; ++k)
+            if (k < a.m) acc[k] = fma(x1, a.y[k][e + stride], fma(x0, a.y[k][e], acc[k]));
+    }
+    if (e < a.n) {
+        const double x0 = a.x[e];
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+            if (k < a.m) acc[k] = fma(x0, a.y[k][e], acc[k]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        if (k >= a.m) break;
+    for (int k = 0; k < MM; ++k) {
         double v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) sh[warp][k] = v;
@@ -648,30 +716,30 @@ dcsd_status multidot(Ctx* c, const double* x, const double* const* ys_host, int 
     a.m = m;
     a.n = n;
     a.partial = c->red;
-    // 4 blocks per SM, partials m * nblk <= kRedDoubles
-    const int nblk = std::max(1, std::min(4 * std::max(c->num_sms, 1), kRedDoubles / 16));
+    // 8 blocks per SM, partials m * nblk <= kRedDoubles
+    const int nblk = std::max(1, std::min(8 * std::max(c->num_sms, 1), kRedDoubles / 16));
     trace_begin(c, "multidot");
-    k_multidot_partial<<<nblk, 256, 0, c->stream>>>(a);
+    if (m <= 1) k_multidot_partial<1><<<nblk, 256, 0, c->stream>>>(a);
+    else if (m <= 2) k_multidot_partial<2><<<nblk, 256, 0, c->stream>>>(a);
+    else if (m <= 4) k_multidot_partial<4><<<nblk, 256, 0, c->stream>>>(a);
+    else if (m <= 8) k_multidot_partial<8><<<nblk, 256, 0, c->stream>>>(a);
+    else k_multidot_partial<16><<<nblk, 256, 0, c->stream>>>(a);
     k_multidot_final<<<m, 256, 0, c->stream>>>(c->red, nblk, m, out);
     trace_end(c);
     return launch_check(c, "multidot");
 }
 
 // deterministic two-pass dot product
-constexpr int kDotBlocks = 512;
+constexpr int kDotBlocks = 1216;  // 8 blocks of 256 threads on each of 152 SMs
 
+template <typename I>
 __global__ void k_dot_partial(EwArgs a, const double* B, double* partial) {
     __shared__ double sh[256];
     double s = 0.0;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.total;
          e += (long)gridDim.x * blockDim.x) {
-        long idx = e, oa = 0, ob = 0;
-        for (int j = a.rank - 1; j >= 0; --j) {
-            long q = idx / a.size[j], r = idx - q * a.size[j];
-            oa += r * a.sa[j];
-            ob += r * a.sc[j];
-            idx = q;
-        }
+        long oa, ob;
+        ew_offsets<I>(a, (I)e, oa, ob);
         s = fma(a.A[oa], B[ob], s);
     }
     sh[threadIdx.x] = s;
@@ -702,7 +770,8 @@ dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accum
     a.A = A.p;
     a.C = nullptr;
     if (c->trace) trace_begin(c, "dot n=" + std::to_string(a.total));
-    k_dot_partial<<<kDotBlocks, 256, 0, c->stream>>>(a, B.p, c->red);
+    if (a.total < (1l << 32)) k_dot_partial<unsigned><<<kDotBlocks, 256, 0, c->stream>>>(a, B.p, c->red);
+    else k_dot_partial<unsigned long><<<kDotBlocks, 256, 0, c->stream>>>(a, B.p, c->red);
     trace_end(c);
     DCSD_TRY(launch_check(c, "dot_partial"));
     k_dot_final<<<1, 256, 0, c->stream>>>(c->red, kDotBlocks, out, accumulate);

@@ -583,6 +583,13 @@ __global__ void __launch_bounds__(256) k_mterm_doubles(MArgs a) {
 // precisions (whose residual error is far above FP32 rounding).
 constexpr int kMaxXFac = 16, kMaxHFac = 8;
 
+// FP64 value in the contraction type (integer-unit conversion for FP32)
+template <typename T> __device__ __forceinline__ T to_t(double x);
+template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_t<float>(double x) { return f64_to_f32(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
     extern __shared__ __align__(16) unsigned char mt_smem[];
@@ -688,16 +695,16 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
     // (3) F_d[a] and G_d[b]
     for (int b = threadIdx.x; b < V && !generic; b += blockDim.x) {
         for (int d = 0; d < nx; ++d) {
-            F[(long)d * V + b] = (T)xd[d].base[(long)b * xd[d].sa];
+            F[(long)d * V + b] = to_t<T>(xd[d].base[(long)b * xd[d].sa]);
             G[(long)d * V + b] = (T)0;
         }
         for (int k = 0; k < nterm; ++k)
             if (grp[k] >= 0)
-                G[(long)grp[k] * V + b] += (T)(coefS[k] * fac[k][1].base[(long)b * fac[k][1].sb]);
+                G[(long)grp[k] * V + b] += to_t<T>(coefS[k] * fac[k][1].base[(long)b * fac[k][1].sb]);
     }
     __syncthreads();
     const double W = *a.W;
-    const T Wt = (T)W;
+    const T Wt = to_t<T>(W);
     const double* t1a = a.t1;
     const double* t1b = a.t1 + O * V;
     const double* c1a = a.c1;
@@ -710,8 +717,8 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
         const bool okx = vir_ok(a, s1, x);
         const bool aa = x == a.vir_act[s1];
         // row-invariant parts of the antisymmetrised t1 c1 product
-        const T tia = (T)tA[i * V + x], cia = (T)cA[i * V + x];
-        const T tja = (T)tA[j * V + x], cja = (T)cA[j * V + x];
+        const T tia = to_t<T>(tA[i * V + x]), cia = to_t<T>(cA[i * V + x]);
+        const T tja = to_t<T>(tA[j * V + x]), cja = to_t<T>(cA[j * V + x]);
         for (int b = threadIdx.x; b < V; b += blockDim.x) {
             const long e = (long)x * V + b;
             const bool okb = vir_ok(a, s2, b);
@@ -725,20 +732,20 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
                 continue;
             }
             T tc;
-            if (blk == 2) tc = tia * (T)c1b[j * V + b] + (T)t1b[j * V + b] * cia;
+            if (blk == 2) tc = tia * to_t<T>(c1b[j * V + b]) + to_t<T>(t1b[j * V + b]) * cia;
             else
-                tc = tia * (T)cB[j * V + b] - tja * (T)cB[i * V + b] - (T)tB[i * V + b] * cja +
-                     (T)tB[j * V + b] * cia;
+                tc = tia * to_t<T>(cB[j * V + b]) - tja * to_t<T>(cB[i * V + b]) - to_t<T>(tB[i * V + b]) * cja +
+                     to_t<T>(tB[j * V + b]) * cia;
             if (x >= 2 && b >= 2 && !generic) {
                 T c2 = (T)0;
                 for (int d = 0; d < nx; ++d) c2 += F[(long)d * V + x] * G[(long)d * V + b];
                 for (int m = 0; m < nh; ++m)
-                    c2 += (T)hc[m] * (T)hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb];
-                Rrow[e] -= (double)(Wt * (c2 - tc));
+                    c2 += to_t<T>(hc[m]) * to_t<T>(hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb]);
+                Rrow[e] -= to_f64(Wt * (c2 - tc));
             } else {
                 const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
                 const int q[4] = {i, j, x, b};
-                Rrow[e] -= W * (eval_class(a, cls, q) - (double)tc);
+                Rrow[e] -= W * (eval_class(a, cls, q) - to_f64(tc));
             }
         }
     }

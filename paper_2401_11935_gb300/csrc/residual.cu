@@ -79,6 +79,26 @@ __global__ void k_energy_combine(double* s) {
     s[1] = s[1] + 0.5 * (s[2] + s[5] - s[6] + s[3] + s[7] - s[8]) + s[4] + s[9];
 }
 
+__global__ void __launch_bounds__(256) k_merge_r2f(long n, const float* __restrict__ f, double* __restrict__ R) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    for (; e + stride < n; e += 2 * stride) {
+        const float f0 = f[e], f1 = f[e + stride];
+        const double r0 = R[e], r1 = R[e + stride];
+        R[e] = r0 + f32_to_f64(f0);
+        R[e + stride] = r1 + f32_to_f64(f1);
+    }
+    if (e < n) R[e] += f32_to_f64(f[e]);
+}
+
+dcsd_status merge_r2f(Ctx* c) {
+    const long n = 3l * c->O * c->O * c->V * c->V;
+    trace_begin(c, "merge_r2f");
+    k_merge_r2f<<<(unsigned)std::max(1, c->num_sms * 8), 256, 0, c->stream>>>(n, c->r2f, c->R2);
+    trace_end(c);
+    return launch_check(c, "merge_r2f");
+}
+
 dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
     const double x = method == DCSD_CCSD ? 1.0 : 0.0;
@@ -90,8 +110,10 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         if (prec == DCSD_PREC_FP64) return einsum64(c, spec, alpha, A, Bm, beta, C);
         return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
     };
-    // small contractions stay FP64; in the tensor-core modes large unbatched
-    // ones (>= 4 GFLOP) go to the tensor cores like the named big ones
+    // small contractions: FP64 in the FP64 mode; in the tensor-core modes
+    // large unbatched ones (>= 4 GFLOP) go to the tensor cores like the named
+    // big ones and the rest use FP32 products (the FP64 units of this GPU run
+    // at a small fraction of its FP32 rate)
     auto sml = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
                    const TV& C) -> dcsd_status {
         if (prec != DCSD_PREC_FP64) {
@@ -100,6 +122,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
             if (plan_einsum(spec, A, Bm, C, p, e) && p.NB == 1 && p.K >= 16 &&
                 2.0 * (double)p.M * (double)p.N * (double)p.K >= 4e9)
                 return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
+            return einsum32(c, spec, alpha, A, Bm, beta, C);
         }
         return einsum64(c, spec, alpha, A, Bm, beta, C);
     };
@@ -169,6 +192,23 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     DCSD_TRY(big("kica,Lkc->Lia", 1.0, blk(t2, 2), Bov, 1.0, blk(Z, 1)));
 
     DCSD_CUDA(c, cudaMemsetAsync(c->R2, 0, sizeof(double) * 3 * O * O * V * V, c->stream));
+    // tensor-core modes: accumulate the tensor-core contributions to R2 in FP32
+    struct R2fGuard {
+        Ctx* c;
+        ~R2fGuard() { c->r2f_on = false; }
+    } r2f_guard{c};
+    if (prec != DCSD_PREC_FP64) {
+        if (!c->r2f) {
+            if (cudaMalloc((void**)&c->r2f, sizeof(float) * 3 * O * O * V * V) != cudaSuccess) {
+                cudaGetLastError();
+                c->r2f = nullptr;
+                c->err = "cudaMalloc of the FP32 residual accumulator failed";
+                return DCSD_ERR_OOM;
+            }
+        }
+        DCSD_CUDA(c, cudaMemsetAsync(c->r2f, 0, sizeof(float) * 3 * O * O * V * V, c->stream));
+        c->r2f_on = true;
+    }
     const int s1_of[3] = {0, 1, 0}, s2_of[3] = {0, 1, 1};
 
     // ---- <ab||ij> (dressed) -------------------------------------------------
@@ -306,7 +346,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         DCSD_TRY(sml("kc,kica->ia", 1.0, fdOV(0), blk(t2, 2), 1.0, blk(R1, 1)));
     }
 
-    // ---- energy Delta E_A (Eq. 2) ----------------------------------------------
+    // ---- energy Delta E_A (Eq. 2), FP64 in every precision mode ------------------
     {
         double* s = c->scal;
         for (int sp = 0; sp < 2; ++sp) {
@@ -316,15 +356,20 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         for (int b = 0; b < 3; ++b) DCSD_TRY(dot_view(c, J, blk(t2, b), s + 2 + b, 0.0));
         TV u = view(c->fsc + 5 * nn2, {O, V});
         for (int sp = 0; sp < 2; ++sp) {
-            DCSD_TRY(sml("ijab,jb->ia", 1.0, J, blk(t1, sp), 0.0, u));
+            DCSD_TRY(einsum64(c, "ijab,jb->ia", 1.0, J, blk(t1, sp), 0.0, u));
             DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 5 + 2 * sp, 0.0));
-            DCSD_TRY(sml("ijab,ja->ib", 1.0, J, blk(t1, sp), 0.0, u));
+            DCSD_TRY(einsum64(c, "ijab,ja->ib", 1.0, J, blk(t1, sp), 0.0, u));
             DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 6 + 2 * sp, 0.0));
         }
-        DCSD_TRY(sml("ijab,jb->ia", 1.0, J, blk(t1, 1), 0.0, u));
+        DCSD_TRY(einsum64(c, "ijab,jb->ia", 1.0, J, blk(t1, 1), 0.0, u));
         DCSD_TRY(dot_view(c, u, blk(t1, 0), s + 9, 0.0));
         k_energy_combine<<<1, 1, 0, c->stream>>>(s);
         DCSD_TRY(launch_check(c, "energy_combine"));
+    }
+
+    if (c->r2f_on) {
+        c->r2f_on = false;
+        DCSD_TRY(merge_r2f(c));
     }
 
     // ---- W = R^X at the A->B double; two-determinant terms ------------------------

@@ -138,10 +138,12 @@ __device__ __forceinline__ __nv_bfloat16 split_part(float x, int part) {
 }
 
 struct TcEpi {
-    int mode;               // 0: FP64 C (alpha, beta); 1: BF16 packed output;
+    int mode;               // 0: FP64 C (alpha, beta); 4: FP32 C32 += alpha * acc;
+                            // 1: BF16 packed output;
                             // 2: ladder producer tile, staged through shared memory
                             //    and stored as 16-byte vectors (see ladder_tc)
     double* C;
+    float* C32;             // mode 4 output; mode 3: FP32 scatter target when set
     __nv_bfloat16* P;
     double alpha, beta;
     int nm, nn;
@@ -160,7 +162,28 @@ struct TcEpi {
     //         s = 2 (ab):           R[2][ij][a][b] += v
     //         s = 3 (ab, (c,d) exchanged): R[2][ij][b][a] += v  (b > a)
     long a0, OO, VV;
+    long O;
+    const int* rowcode;     // mode 3: row -> (block << 20 | i << 10 | j); same-spin rows are pairs i < j
+    const long* mrow;       // modes 0/4: row -> offset in C (replaces the m-mode decomposition)
 };
+
+// ladder consumer scatter of one accumulator element v = W(a,b) for the row
+// (blk, i, j); same-spin blocks hold the pair i < j only and also fill the
+// (j, i) row: R[ij][ab] = -R[ij][ba] = -R[ji][ab] = R[ji][ba]
+template <typename T>
+__device__ __forceinline__ void ladder_scatter(T* R, int sblk, long ro1, long ro2, long a, long b, long V, T v) {
+    if (b < a) return;
+    if (sblk < 2) {
+        R[ro1 + a * V + b] += v;
+        R[ro1 + b * V + a] -= v;
+        R[ro2 + a * V + b] -= v;
+        R[ro2 + b * V + a] += v;
+    } else if (sblk == 2) {
+        R[ro1 + a * V + b] += v;
+    } else if (b > a) {
+        R[ro1 + b * V + a] += v;
+    }
+}
 
 __device__ __forceinline__ long decomp1(long idx, int nmode, const long* size, const long* s) {
     long o = 0;
@@ -350,9 +373,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             } else if (epi.mode == 3) {
                 const long m = (long)m0 + 32 * q + lane;
                 const bool rowok = m < epi.M;
-                const int sblk = (int)(m / epi.OO);
-                const long ij = m - (long)sblk * epi.OO;
-                double* Rb = epi.C + (long)(sblk < 2 ? sblk : 2) * epi.OO * epi.VV + ij * epi.VV;
+                const int code = rowok ? epi.rowcode[m] : 0;
+                const int sblk = code >> 20, ri = (code >> 10) & 1023, rj = code & 1023;
+                const long blkoff = (long)(sblk < 2 ? sblk : 2) * epi.OO * epi.VV;
+                const long ro1 = blkoff + ((long)ri * epi.O + rj) * epi.VV;
+                const long ro2 = blkoff + ((long)rj * epi.O + ri) * epi.VV;
 #pragma unroll 1
                 for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t r[32];
@@ -364,17 +389,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int jj = 0; jj < 32; ++jj) {
                         if (nst + jj < epi.N) {
                             const long a = epi.a0 + rr, b = epi.a0 + bb;
-                            const double v = (double)__uint_as_float(r[jj]);
-                            if (b >= a) {
-                                if (sblk < 2) {
-                                    Rb[a * epi.V + b] += v;
-                                    Rb[b * epi.V + a] -= v;
-                                } else if (sblk == 2) {
-                                    Rb[a * epi.V + b] += v;
-                                } else if (b > a) {
-                                    Rb[b * epi.V + a] += v;
-                                }
-                            }
+                            if (epi.C32)
+                                ladder_scatter<float>(epi.C32, sblk, ro1, ro2, a, b, epi.V, __uint_as_float(r[jj]));
+                            else
+                                ladder_scatter<double>(epi.C, sblk, ro1, ro2, a, b, epi.V,
+                                                       (double)__uint_as_float(r[jj]));
                         }
                         if (++bb == epi.Vb) { bb = 0; ++rr; }
                     }
@@ -382,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             } else {
                 const long m = (long)m0 + 32 * q + lane;
                 const bool rowok = m < epi.M;
-                const long roff = rowok ? decomp1(m, epi.nm, epi.m_size, epi.m_s) : 0;
+                const long roff = !rowok ? 0 : epi.mrow ? epi.mrow[m] : decomp1(m, epi.nm, epi.m_size, epi.m_s);
                 const float alpha = (float)epi.alpha;
 #pragma unroll 1
                 for (int ch = ch0; ch < ch1; ++ch) {
@@ -407,42 +426,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             }
                         }
                     }
-                    // offsets of the 32 columns (distinct addresses)
-                    long offs[32];
+                    // two halves of 16 columns (keeps the offset and old-value
+                    // arrays in registers)
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        offs[jj] = ((long)n0 + ch * 32 + jj < epi.N) ? roff + coff : -1;
+                    for (int h = 0; h < 2; ++h) {
+                        long offs[16];
 #pragma unroll
-                        for (int k = kMaxMode - 1; k >= 0; --k) {
-                            if (k < epi.nn) {
-                                coff += epi.n_s[k];
-                                if (++ci[k] < epi.n_size[k]) break;
-                                coff -= ci[k] * epi.n_s[k];
-                                ci[k] = 0;
+                        for (int jj = 0; jj < 16; ++jj) {
+                            offs[jj] = ((long)n0 + ch * 32 + h * 16 + jj < epi.N) ? roff + coff : -1;
+#pragma unroll
+                            for (int k = kMaxMode - 1; k >= 0; --k) {
+                                if (k < epi.nn) {
+                                    coff += epi.n_s[k];
+                                    if (++ci[k] < epi.n_size[k]) break;
+                                    coff -= ci[k] * epi.n_s[k];
+                                    ci[k] = 0;
+                                }
                             }
                         }
-                    }
-                    if (epi.mode == 0) {
-                        // read all accumulated values first, then write: keeps
-                        // the 32 loads in flight instead of load/store pairs
-                        double old[32];
-                        if (epi.beta != 0.0) {
+                        if (epi.mode == 4) {
+                            float oldf[16];
 #pragma unroll
-                            for (int jj = 0; jj < 32; ++jj) old[jj] = offs[jj] >= 0 ? epi.C[offs[jj]] : 0.0;
-                        }
+                            for (int jj = 0; jj < 16; ++jj) oldf[jj] = offs[jj] >= 0 ? epi.C32[offs[jj]] : 0.0f;
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            if (offs[jj] < 0) continue;
-                            const double v = (double)(alpha * __uint_as_float(r[jj]));
-                            epi.C[offs[jj]] = epi.beta != 0.0 ? fma(epi.beta, old[jj], v) : v;
-                        }
-                    } else {
+                            for (int jj = 0; jj < 16; ++jj)
+                                if (offs[jj] >= 0) epi.C32[offs[jj]] = fmaf(alpha, __uint_as_float(r[h * 16 + jj]), oldf[jj]);
+                        } else if (epi.mode == 0) {
+                            // all loads of the half first, then the stores
+                            double old[16];
+                            if (epi.beta != 0.0) {
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            if (offs[jj] < 0) continue;
-                            const float v = alpha * __uint_as_float(r[jj]);
-                            for (int sgm = 0; sgm < epi.nseg; ++sgm)
-                                epi.P[offs[jj] + sgm * epi.segstride] = split_part(v, epi.pat[sgm]);
+                                for (int jj = 0; jj < 16; ++jj) old[jj] = offs[jj] >= 0 ? epi.C[offs[jj]] : 0.0;
+                            }
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                if (offs[jj] < 0) continue;
+                                const double v = (double)(alpha * __uint_as_float(r[h * 16 + jj]));
+                                epi.C[offs[jj]] = epi.beta != 0.0 ? fma(epi.beta, old[jj], v) : v;
+                            }
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                if (offs[jj] < 0) continue;
+                                const float v = alpha * __uint_as_float(r[h * 16 + jj]);
+                                for (int sgm = 0; sgm < epi.nseg; ++sgm)
+                                    epi.P[offs[jj] + sgm * epi.segstride] = split_part(v, epi.pat[sgm]);
+                            }
                         }
                     }
                 }
@@ -474,6 +503,7 @@ struct PackArgs {
     long k_size[kMaxMode], k_s[kMaxMode];
     int kfast;  // source contiguous along k
     long rvalid, kvalid;  // innermost row / k mode indices >= these read as 0
+    const long* rtab;     // if set: row -> source offset (replaces the row modes)
 };
 
 // offset of a linear index over up to kMaxMode modes (last mode fastest);
@@ -508,7 +538,8 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
             long o = -1;
             if (r < a.rows) {
                 const unsigned ru = (unsigned)r;
-                if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
+                if (a.rtab) o = a.rtab[r];
+                else if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
                     o = decomp1_u32(ru, a.nr, a.r_size, a.r_s);
             }
             roff[threadIdx.x] = o;
@@ -530,7 +561,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
             if (a.kfast) { kk = e & 63; rr = e >> 6; }
             else { rr = e & 63; kk = e >> 6; }
             const long ro = roff[rr], ko = koff[kk];
-            tile[rr][kk] = (ro >= 0 && ko >= 0) ? (float)a.src[ro + ko] : 0.0f;
+            tile[rr][kk] = (ro >= 0 && ko >= 0) ? f64_to_f32(a.src[ro + ko]) : 0.0f;
         }
         __syncthreads();
         // 64 rows x 8 groups of 8 k: 8 consecutive threads cover one row
@@ -568,6 +599,11 @@ struct TcEngine {
     int* d_err = nullptr;
     Buf pa, pb, pv, pt;  // generic A, generic B, ladder V tile, stacked amplitudes
     bool attr_set = false;
+    // ladder row tables for the stacked amplitudes [aa pairs; bb pairs; ab; ab~]
+    long tab_O = -1, tab_V = -1;
+    long* d_pairoff = nullptr;  // [2P] t2 offset of the same-spin pair rows
+    int* d_rowcode = nullptr;   // [rows] block/i/j code of every row
+    long* d_growoff = nullptr;  // [rows] offset of the row's G[blk][i][j] slice
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -606,6 +642,9 @@ void tc_free(Ctx* c) {
     if (!e) return;
     for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt})
         if (b->p) cudaFree(b->p);
+    if (e->d_pairoff) cudaFree(e->d_pairoff);
+    if (e->d_rowcode) cudaFree(e->d_rowcode);
+    if (e->d_growoff) cudaFree(e->d_growoff);
     delete e;
     c->tc = nullptr;
 }
@@ -631,8 +670,9 @@ static dcsd_status make_map(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, lo
 static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
                         const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
                         const int* pat, __nv_bfloat16* dst, long rvalid = 1l << 62,
-                        long kvalid = 1l << 62) {
+                        long kvalid = 1l << 62, const long* rtab = nullptr) {
     PackArgs a;
+    a.rtab = rtab;
     a.rvalid = rvalid;
     a.kvalid = kvalid;
     a.src = src;
@@ -694,9 +734,14 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     size_t smem = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
     const int cls = c->ladder_phase ? DCSD_PROF_LADDER : DCSD_PROF_TC_OTHER;
     prof_begin(c, cls);
-    if (c->trace)
-        trace_begin(c, std::string(c->ladder_phase ? "tc-ladder " : "tc ") + c->cur_spec + " mode=" + std::to_string(epi.mode) +
-                           " M=" + std::to_string(M) + " N=" + std::to_string(N) + " Kt=" + std::to_string(Ktot));
+    if (c->trace) {
+        const std::string label = std::string(c->ladder_phase ? "tc-ladder " : "tc ") + c->cur_spec +
+                                  " mode=" + std::to_string(epi.mode) + " M=" + std::to_string(M) +
+                                  " N=" + std::to_string(N) + " Kt=" + std::to_string(Ktot);
+        if (c->trace_seq) fprintf(stderr, "[dcsd tc #%d] %s\n", c->tc_seq, label.c_str());
+        trace_begin(c, label);
+    }
+    ++c->tc_seq;
     if (BN == 256)
         k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
     else
@@ -792,6 +837,12 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
     epi.C = C.p;
     epi.alpha = alpha;
     epi.beta = beta;
+    // accumulation into R2 goes to its FP32 shadow while that is active
+    const size_t r2len = 3ul * c->O * c->O * c->V * c->V;
+    if (c->r2f_on && beta == 1.0 && C.p >= c->R2 && C.p < c->R2 + r2len) {
+        epi.mode = 4;
+        epi.C32 = c->r2f + (C.p - c->R2);
+    }
     epi.nm = p.nm;
     epi.nn = p.nn;
     for (int i = 0; i < kMaxMode; ++i) {
@@ -814,6 +865,51 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
 // amplitudes [(s,i,j)][(c,d)]; the integrals are never stored beyond one
 // chunk.  ab~ is the alpha-beta block with (c,d) exchanged.
 // ---------------------------------------------------------------------------
+// G[s][j][i] = -G[s][i][j] (i < j) and G[s][i][i] = 0 for the same-spin
+// blocks s = 0, 1 of G[4][O][O][O][V]
+__global__ void k_mirror_pairs(long O, long OV, double* G) {
+    const long per = O * O * OV;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < 2 * per; e += (long)gridDim.x * blockDim.x) {
+        const long s = e / per, r = e - s * per;
+        const long ij = r / OV, kb = r - ij * OV;
+        const long i = ij / O, j = ij - i * O;
+        if (i < j) continue;
+        double* Gs = G + s * per;
+        Gs[r] = i == j ? 0.0 : -Gs[(j * O + i) * OV + kb];
+    }
+}
+
+// Chunks [r0, r0 + nr) of the ladder's first virtual index, nr <= nmax,
+// chosen by dynamic programming to minimise the k-steps of the busiest SM
+// over the producer and consumer GEMMs of all chunks (each GEMM runs
+// ceil(tiles / SMs) waves of tiles of equal work).
+static std::vector<std::pair<long, long>> ladder_chunks(long V, long Vp, long rows, long K2t, long Xt, long nmax,
+                                                        int sms) {
+    auto waves = [&](long M, long N) {
+        const long bn = N >= 256 ? 256 : 128;
+        const long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + bn - 1) / bn);
+        return (tiles + sms - 1) / sms;
+    };
+    const double launch = 64.0;  // fixed cost of a launch pair, in k-steps
+    std::vector<double> best(V + 1, 0.0);
+    std::vector<long> pick(V + 1, 1);
+    for (long r0 = V - 1; r0 >= 0; --r0) {
+        best[r0] = 1e300;
+        for (long nr = 1; nr <= std::min(nmax, V - r0); ++nr) {
+            const long Vb = V - r0;
+            const double cost = (double)waves(rows, nr * Vb) * (double)(K2t / TC_BK) +
+                                (double)waves(nr * V, Vb * Vp) * (double)(Xt / TC_BK) + launch + best[r0 + nr];
+            if (cost < best[r0]) {
+                best[r0] = cost;
+                pick[r0] = nr;
+            }
+        }
+    }
+    std::vector<std::pair<long, long>> out;
+    for (long r0 = 0; r0 < V; r0 += pick[r0]) out.push_back({r0, pick[r0]});
+    return out;
+}
+
 dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     TcEngine* e = c->tc;
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
@@ -824,17 +920,58 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     const long Vp = round_up(V, 8);
     const long K2 = V * Vp, K2p = round_up(K2, TC_BK), K2t = nseg * K2p;
     const long XP = round_up(X, TC_BK), Xt = nseg * XP;
-    const long rows4 = 4 * O * O;
-    // stacked amplitudes [aa; bb; ab; ab~] x (c,d)
+    // stacked amplitude rows: the same-spin blocks are antisymmetric in (i,j),
+    // so only their pairs i < j are contracted
+    const long P = O * (O - 1) / 2;
+    const long rows4 = 2 * P + 2 * O * O;
+    if (O >= 1024) {
+        c->err = "ladder row codes hold occupied indices below 1024";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    if (e->tab_O != O || e->tab_V != V) {
+        std::vector<long> pairoff(2 * P > 0 ? 2 * P : 1), growoff(rows4);
+        std::vector<int> code(rows4);
+        long m = 0;
+        for (int s = 0; s < 2; ++s)
+            for (long i = 0; i < O; ++i)
+                for (long j = i + 1; j < O; ++j, ++m) {
+                    pairoff[m] = ((long)s * O * O + i * O + j) * V * V;
+                    code[m] = (s << 20) | (int)(i << 10) | (int)j;
+                    growoff[m] = ((long)s * O * O + i * O + j) * O * V;
+                }
+        for (int s = 2; s < 4; ++s)
+            for (long i = 0; i < O; ++i)
+                for (long j = 0; j < O; ++j, ++m) {
+                    code[m] = (s << 20) | (int)(i << 10) | (int)j;
+                    growoff[m] = ((long)s * O * O + i * O + j) * O * V;
+                }
+        for (long** pp : {&e->d_pairoff, &e->d_growoff})
+            if (*pp) { cudaFree(*pp); *pp = nullptr; }
+        if (e->d_rowcode) { cudaFree(e->d_rowcode); e->d_rowcode = nullptr; }
+        e->tab_O = e->tab_V = -1;
+        DCSD_CUDA(c, cudaMalloc((void**)&e->d_pairoff, sizeof(long) * pairoff.size()));
+        DCSD_CUDA(c, cudaMalloc((void**)&e->d_growoff, sizeof(long) * rows4));
+        DCSD_CUDA(c, cudaMalloc((void**)&e->d_rowcode, sizeof(int) * rows4));
+        DCSD_CUDA(c, cudaMemcpy(e->d_pairoff, pairoff.data(), sizeof(long) * pairoff.size(), cudaMemcpyHostToDevice));
+        DCSD_CUDA(c, cudaMemcpy(e->d_growoff, growoff.data(), sizeof(long) * rows4, cudaMemcpyHostToDevice));
+        DCSD_CUDA(c, cudaMemcpy(e->d_rowcode, code.data(), sizeof(int) * rows4, cudaMemcpyHostToDevice));
+        e->tab_O = O;
+        e->tab_V = V;
+    }
+    // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d)
     DCSD_TRY(ensure(c, e->pt, (size_t)rows4 * K2t));
     {
-        long rsz[1] = {3 * O * O}, rs[1] = {V * V};
+        long rs[1] = {V * V};
         long ksz[2] = {V, Vp}, ks[2] = {V, 1};
-        DCSD_TRY(pack(c, c->t2, 1, rsz, rs, 2, ksz, ks, 3 * O * O, K2, K2p, nseg, pa, e->pt.p, 1l << 62, V));
+        if (P > 0)
+            DCSD_TRY(pack(c, c->t2, 0, nullptr, nullptr, 2, ksz, ks, 2 * P, K2, K2p, nseg, pa, e->pt.p, 1l << 62, V,
+                          e->d_pairoff));
         long rsz2[1] = {O * O};
+        DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks, O * O, K2, K2p, nseg, pa,
+                      e->pt.p + (size_t)2 * P * K2t, 1l << 62, V));
         long ks2[2] = {1, V};  // (c,d) -> t_ab[ij][d][c]
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks2, O * O, K2, K2p, nseg, pa,
-                      e->pt.p + (size_t)3 * O * O * K2t, 1l << 62, V));
+                      e->pt.p + (size_t)(2 * P + O * O) * K2t, 1l << 62, V));
     }
     // B_vv packed as [(b,d)][L], d padded (constant over the chunk loop)
     DCSD_TRY(ensure(c, e->pb, (size_t)K2 * Xt));
@@ -858,8 +995,12 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     // rows with (c,d) exchanged and same-spin blocks are antisymmetric.
     for (int pass = 0; pass < 2; ++pass) {
         const long R = pass == 0 ? V : O;
-        for (long r0 = 0; r0 < R; r0 += chunk) {
-            const long nr = std::min(chunk, R - r0);
+        std::vector<std::pair<long, long>> chunks;
+        if (pass == 0) chunks = ladder_chunks(V, Vp, rows4, K2t, Xt, chunk, c->num_sms);
+        else
+            for (long r0 = 0; r0 < R; r0 += chunk) chunks.push_back({r0, std::min(chunk, R - r0)});
+        for (const auto& ck : chunks) {
+            const long r0 = ck.first, nr = ck.second;
             const long b0 = pass == 0 ? r0 : 0;  // first b column built
             const long Vb = V - b0;
             // producer A: rows (r,c) of B_L[row][c] -> [(r,c)][L]
@@ -894,6 +1035,9 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
             if (pass == 0) {
                 ce.mode = 3;
                 ce.C = R2;
+                ce.C32 = (c->r2f_on && R2 == c->R2) ? c->r2f : nullptr;
+                ce.rowcode = e->d_rowcode;
+                ce.O = O;
                 ce.V = V;
                 ce.Vb = Vb;
                 ce.a0 = r0;
@@ -901,8 +1045,9 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 ce.VV = V * V;
                 DCSD_TRY(gemm_packed(c, e->pt.p, rows4, e->pv.p, nr * Vb, K2t, ce));
             } else {
-                ce.C = G + r0 * V;       // G[s][i][j][k][b], rows (s,i,j) stride O*V
+                ce.C = G + r0 * V;       // G[s][i][j][k][b], row (s,i,j) at the table's offset
                 ce.beta = 0.0;
+                ce.mrow = e->d_growoff;
                 ce.m_size[0] = rows4; ce.m_s[0] = O * V;
                 ce.n_size[0] = nr; ce.n_s[0] = V;
                 ce.n_size[1] = V;  ce.n_s[1] = 1;
@@ -910,7 +1055,9 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
             }
         }
     }
-    return DCSD_OK;
+    // the same-spin G rows (j,i) and (i,i)
+    k_mirror_pairs<<<(unsigned)std::max(1, c->num_sms * 8), 256, 0, c->stream>>>(O, O * V, G);
+    return launch_check(c, "mirror_pairs");
 }
 
 }  // namespace dcsd
