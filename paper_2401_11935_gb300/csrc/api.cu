@@ -33,6 +33,10 @@ __device__ __forceinline__ double recip_nr(double D) {
 // virtual diagonal Fock elements of the row's spins are staged in shared
 // memory (2*V doubles of dynamic shared memory, or read from the Fock
 // matrices when stage is false).
+// F32: the doubles' step -R/D is formed in FP32 (tensor-core precisions;
+// the step only has to be a good preconditioned direction, the update
+// t + step and the stored vectors stay FP64)
+template <bool F32>
 __global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V, const double* fa,
                                                      const double* fb, const double* t, const double* R,
                                                      double* tnew, double* step, bool stage) {
@@ -94,7 +98,14 @@ __global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V
                     const unsigned e = e0 + q * bs;
                     if (e >= VV) break;
                     const unsigned x = e / (unsigned)V, b = e - x * (unsigned)V;
-                    const double st = r[q] != 0.0 ? -r[q] * recip_nr(d1[x * d1s] - dij + d2[b * d2s]) : 0.0;
+                    double st;
+                    if (F32) {
+                        const float rf = f64_to_f32(r[q]);
+                        const float Df = f64_to_f32(d1[x * d1s] - dij) + f64_to_f32(d2[b * d2s]);
+                        st = rf != 0.0f ? f32_to_f64(-rf * __frcp_rn(Df)) : 0.0;
+                    } else {
+                        st = r[q] != 0.0 ? -r[q] * recip_nr(d1[x * d1s] - dij + d2[b * d2s]) : 0.0;
+                    }
                     step[base + e] = st;
                     tnew[base + e] = tt[q] + st;
                 }
@@ -627,9 +638,13 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         {
             const size_t jsm = 2ul * c->V * sizeof(double);
             const bool stage = jsm <= 48 * 1024;
-            k_jacobi_rows<<<(unsigned)std::min<long>(2l * c->O + 3l * c->O * c->O, (long)c->num_sms * 8), 256,
-                            stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, c->t1, c->R1, tn_v,
-                                                          st_v, stage);
+            const unsigned jg = (unsigned)std::min<long>(2l * c->O + 3l * c->O * c->O, (long)c->num_sms * 8);
+            if (prec == DCSD_PREC_FP64)
+                k_jacobi_rows<false><<<jg, 256, stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb,
+                                                                               c->t1, c->R1, tn_v, st_v, stage);
+            else
+                k_jacobi_rows<true><<<jg, 256, stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb,
+                                                                              c->t1, c->R1, tn_v, st_v, stage);
         }
         trace_end(c);
         if ((s = launch_check(c, "jacobi")) != DCSD_OK) { status = s; break; }

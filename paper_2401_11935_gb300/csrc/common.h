@@ -122,6 +122,7 @@ struct Ctx {
     bool trace = false;
     bool trace_seq = false;  // also list every tensor-core GEMM launch in order
     int tc_seq = 0;          // tensor-core GEMM launches so far
+    int pack_seq = 0;        // operand pack launches so far
     bool verbose = false;         // DCSD_VERBOSE=1: per-iteration solver log on stderr
     std::string cur_spec;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;

@@ -234,23 +234,31 @@ struct GemmArgs {
     double* ws;
 };
 
+// linear index -> two offsets; every decomposed index (m, n, k, batch) is
+// below 2^31 (checked on the host), so the divisions are 32-bit
 __device__ __forceinline__ void decomp2(long idx, int nmode, const long* size, const long* s1,
                                         const long* s2, long& o1, long& o2) {
     o1 = 0;
     o2 = 0;
+    unsigned u = (unsigned)idx;
 #pragma unroll
     for (int j = kMaxMode - 1; j >= 0; --j) {
         if (j < nmode) {
-            long q = idx / size[j];
-            long r = idx - q * size[j];
-            o1 += r * s1[j];
-            o2 += r * s2[j];
-            idx = q;
+            const unsigned sz = (unsigned)size[j];
+            const unsigned q = u / sz, r = u - q * sz;
+            o1 += (long)r * s1[j];
+            o2 += (long)r * s2[j];
+            u = q;
         }
     }
 }
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+// FP64 input in the product type (integer-unit conversion for FP32)
+template <typename T> __device__ __forceinline__ T cvt_in(double x);
+template <> __device__ __forceinline__ double cvt_in<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt_in<float>(double x) { return f64_to_f32(x); }
 
 // T = double: FP64 products and accumulation.  T = float: FP32 products of
 // the FP64 inputs (each loaded element is converted once and reused across
@@ -307,14 +315,14 @@ __global__ void __launch_bounds__(256) k_gemm_t(GemmArgs g) {
                 if (g.a_kfast) { kk = e % GBK; mm = e / GBK; }
                 else { mm = e % GBM; kk = e / GBM; }
                 long ra = rA[mm], ka = kA[kk];
-                As[kk][mm] = (ra >= 0 && ka >= 0) ? (T)g.A[oA + ra + ka] : (T)0;
+                As[kk][mm] = (ra >= 0 && ka >= 0) ? cvt_in<T>(g.A[oA + ra + ka]) : (T)0;
             }
             for (int e = tid; e < GBN * GBK; e += 256) {
                 int nn, kk;
                 if (g.b_kfast) { kk = e % GBK; nn = e / GBK; }
                 else { nn = e % GBN; kk = e / GBN; }
                 long cb = cB[nn], kb = kB[kk];
-                Bs[kk][nn] = (cb >= 0 && kb >= 0) ? (T)g.B[oB + cb + kb] : (T)0;
+                Bs[kk][nn] = (cb >= 0 && kb >= 0) ? cvt_in<T>(g.B[oB + cb + kb]) : (T)0;
             }
             __syncthreads();
             T part[4][4];
@@ -439,6 +447,10 @@ static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV&
         return DCSD_ERR_INVALID_ARG;
     }
     if (g.p.M == 0 || g.p.N == 0 || g.p.NB == 0) return DCSD_OK;
+    if (g.p.M >= (1l << 31) || g.p.N >= (1l << 31) || g.p.K >= (1l << 31) || g.p.NB >= (1l << 31)) {
+        c->err = std::string(spec) + ": contraction extent beyond 2^31";
+        return DCSD_ERR_INVALID_ARG;
+    }
     g.A = A.p;
     g.B = B.p;
     g.C = C.p;
@@ -464,7 +476,9 @@ static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV&
     const long tiles = ((g.p.M + GBM - 1) / GBM) * ((g.p.N + GBN - 1) / GBN);
     if (g.p.NB == 1 && tiles < c->num_sms && g.p.K >= 2048 && c->splitk_ws) {
         // few output tiles and a long contraction: split K over CTAs
-        long ns = std::min<long>((2 * c->num_sms + tiles - 1) / tiles, g.p.K / 512);
+        // about 8 blocks of 256 threads per SM: enough loads in flight to
+        // stream the long operands
+        long ns = std::min<long>((8 * c->num_sms + tiles - 1) / tiles, g.p.K / 256);
         ns = std::min<long>(ns, (long)(c->splitk_elems / std::max<long>(1, g.p.M * g.p.N)));
         ns = std::min<long>(ns, 65535);
         if (ns >= 2) {

@@ -713,41 +713,77 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
     const double* cA = blk == 1 ? c1b : c1a;
     const double* tB = blk == 0 ? t1a : t1b;  // spin of b (s2)
     const double* cB = blk == 0 ? c1a : c1b;
-    for (int x = 0; x < V; ++x) {
+    // b-dependent factors of the antisymmetrised t1 c1 product, in T:
+    // cj[b] = c_jb, tj[b] = t_jb, ci[b] = c_ib, ti[b] = t_ib (spin of b)
+    T* cj = G + (long)maxx * V;
+    T* tj = cj + V;
+    T* ci = tj + V;
+    T* ti = ci + V;
+    __shared__ T hcT[kMaxHFac];
+    for (int b = threadIdx.x; b < V; b += blockDim.x) {
+        cj[b] = to_t<T>(cB[j * V + b]);
+        tj[b] = to_t<T>(tB[j * V + b]);
+        ci[b] = to_t<T>(cB[i * V + b]);
+        ti[b] = to_t<T>(tB[i * V + b]);
+    }
+    if (threadIdx.x < nh) hcT[threadIdx.x] = to_t<T>(hc[threadIdx.x]);
+    __syncthreads();
+    // the element's t1 c1 term (b-independent parts passed in)
+    auto tc_of = [&](int b, T tia, T cia, T tja, T cja) -> T {
+        if (blk == 2) return tia * cj[b] + tj[b] * cia;
+        return tia * cj[b] - tja * ci[b] - ti[b] * cja + tj[b] * cia;
+    };
+    // (4) elements with a and b external: separable form
+    const bool zero_diag = blk != 2;
+    for (int x = 2; x < V; ++x) {
         const bool okx = vir_ok(a, s1, x);
-        const bool aa = x == a.vir_act[s1];
-        // row-invariant parts of the antisymmetrised t1 c1 product
         const T tia = to_t<T>(tA[i * V + x]), cia = to_t<T>(cA[i * V + x]);
         const T tja = to_t<T>(tA[j * V + x]), cja = to_t<T>(cA[j * V + x]);
-        for (int b = threadIdx.x; b < V; b += blockDim.x) {
-            const long e = (long)x * V + b;
-            const bool okb = vir_ok(a, s2, b);
-            if (!okx || !okb || (blk != 2 && x == b)) {
-                Rrow[e] = 0.0;
+        T fx[kMaxXFac];
+#pragma unroll
+        for (int d = 0; d < kMaxXFac; ++d) fx[d] = d < nx ? F[(long)d * V + x] : (T)0;
+        double* Rx = Rrow + (long)x * V;
+        for (int b = 2 + threadIdx.x; b < V; b += blockDim.x) {
+            if (!okx || (zero_diag && x == b)) {
+                Rx[b] = 0.0;
                 continue;
             }
-            const bool ab = b == a.vir_act[s2];
-            if (blk == 2 && ai && aj && aa && ab) {  // the A->B element
-                Rrow[e] = 0.0;
-                continue;
-            }
-            T tc;
-            if (blk == 2) tc = tia * to_t<T>(c1b[j * V + b]) + to_t<T>(t1b[j * V + b]) * cia;
-            else
-                tc = tia * to_t<T>(cB[j * V + b]) - tja * to_t<T>(cB[i * V + b]) - to_t<T>(tB[i * V + b]) * cja +
-                     to_t<T>(tB[j * V + b]) * cia;
-            if (x >= 2 && b >= 2 && !generic) {
-                T c2 = (T)0;
-                for (int d = 0; d < nx; ++d) c2 += F[(long)d * V + x] * G[(long)d * V + b];
+            T c2 = (T)0;
+            if (!generic) {
+#pragma unroll
+                for (int d = 0; d < kMaxXFac; ++d)
+                    if (d < nx) c2 += fx[d] * G[(long)d * V + b];
                 for (int m = 0; m < nh; ++m)
-                    c2 += to_t<T>(hc[m]) * to_t<T>(hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb]);
-                Rrow[e] -= to_f64(Wt * (c2 - tc));
+                    c2 += hcT[m] * to_t<T>(hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb]);
+                Rx[b] -= to_f64(Wt * (c2 - tc_of(b, tia, cia, tja, cja)));
             } else {
-                const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
+                const int cls = blk * 16 + (ai << 3) + (aj << 2);
                 const int q[4] = {i, j, x, b};
-                Rrow[e] -= W * (eval_class(a, cls, q) - to_f64(tc));
+                Rx[b] -= W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)));
             }
         }
+    }
+    // (5) elements with a or b an open orbital: per-term evaluation
+    for (int e2 = threadIdx.x; e2 < 4 * (int)V; e2 += blockDim.x) {
+        int x, b;
+        if (e2 < 2 * (int)V) { x = e2 / (int)V; b = e2 % (int)V; }          // rows a = 0, 1
+        else { const int r = e2 - 2 * (int)V; b = r / (int)V; x = r % (int)V; if (x < 2) continue; }  // columns b = 0, 1
+        const long e = (long)x * V + b;
+        const bool okx = vir_ok(a, s1, x), okb = vir_ok(a, s2, b);
+        if (!okx || !okb || (zero_diag && x == b)) {
+            Rrow[e] = 0.0;
+            continue;
+        }
+        const bool aa = x == a.vir_act[s1], ab = b == a.vir_act[s2];
+        if (blk == 2 && ai && aj && aa && ab) {  // the A->B element
+            Rrow[e] = 0.0;
+            continue;
+        }
+        const T tia = to_t<T>(tA[i * V + x]), cia = to_t<T>(cA[i * V + x]);
+        const T tja = to_t<T>(tA[j * V + x]), cja = to_t<T>(cA[j * V + x]);
+        const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
+        const int q[4] = {i, j, x, b};
+        Rrow[e] -= W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)));
     }
 }
 
@@ -792,7 +828,7 @@ dcsd_status apply_mterms(Ctx* c, int ref, bool fp32) {
     k_mterm_singles<<<(unsigned)std::max<long>(1, (n1 + 255) / 256), 256, 0, c->stream>>>(a);
     DCSD_TRY(launch_check(c, "mterm_singles"));
     const int maxx = std::max(g_max_xfac, 1);
-    const size_t smem = 2ul * maxx * c->V * (fp32 ? sizeof(float) : sizeof(double));
+    const size_t smem = (2ul * maxx + 4) * c->V * (fp32 ? sizeof(float) : sizeof(double));
     const unsigned grid = (unsigned)(3l * c->O * c->O);
     trace_begin(c, fp32 ? "mterm_doubles_sep32" : "mterm_doubles_sep64");
     if (g_max_xfac > kMaxXFac || g_max_hfac > kMaxHFac || smem > 160 * 1024) {

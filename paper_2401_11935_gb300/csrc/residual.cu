@@ -110,17 +110,16 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         if (prec == DCSD_PREC_FP64) return einsum64(c, spec, alpha, A, Bm, beta, C);
         return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
     };
-    // small contractions: FP64 in the FP64 mode; in the tensor-core modes
-    // large unbatched ones (>= 4 GFLOP) go to the tensor cores like the named
-    // big ones and the rest use FP32 products (the FP64 units of this GPU run
-    // at a small fraction of its FP32 rate)
+    // small contractions: FP64 in the FP64 mode; in the tensor-core modes the
+    // contraction engine picks the tensor cores (split-K when the output is
+    // small) or, for tiny or batched shapes, FP32 products on the CUDA cores
+    // (the FP64 units of this GPU run at a small fraction of its FP32 rate)
     auto sml = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
                    const TV& C) -> dcsd_status {
         if (prec != DCSD_PREC_FP64) {
             GemmPlan p;
             std::string e;
-            if (plan_einsum(spec, A, Bm, C, p, e) && p.NB == 1 && p.K >= 16 &&
-                2.0 * (double)p.M * (double)p.N * (double)p.K >= 4e9)
+            if (plan_einsum(spec, A, Bm, C, p, e) && p.NB == 1 && p.K >= 16)
                 return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
             return einsum32(c, spec, alpha, A, Bm, beta, C);
         }

@@ -139,6 +139,7 @@ __device__ __forceinline__ __nv_bfloat16 split_part(float x, int part) {
 
 struct TcEpi {
     int mode;               // 0: FP64 C (alpha, beta); 4: FP32 C32 += alpha * acc;
+                            // 5: split-K FP32 partial tiles into C32;
                             // 1: BF16 packed output;
                             // 2: ladder producer tile, staged through shared memory
                             //    and stored as 16-byte vectors (see ladder_tc)
@@ -198,6 +199,22 @@ __device__ __forceinline__ long decomp1(long idx, int nmode, const long* size, c
     return o;
 }
 
+// offset of a linear index over up to kMaxMode modes (last mode fastest);
+// indices and mode sizes are below 2^31, so the divisions are 32-bit
+__device__ __forceinline__ long decomp1_u32(unsigned idx, int nmode, const long* size, const long* s) {
+    long o = 0;
+#pragma unroll
+    for (int j = kMaxMode - 1; j >= 0; --j) {
+        if (j < nmode) {
+            const unsigned sz = (unsigned)size[j];
+            const unsigned q = idx / sz;
+            o += (long)(idx - q * sz) * s[j];
+            idx = q;
+        }
+    }
+    return o;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -212,7 +229,7 @@ constexpr int kStageBytesMode2 = kEpiWarps * 32 * 64 * 2;  // epilogue staging, 
 template <int BN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
-              int nkt, int tilesM, int tilesN, int* err) {
+              int nkt, int tilesM, int tilesN, int kper, int* err) {
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
     constexpr uint32_t STAGE = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
@@ -227,7 +244,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int* consumed = issued + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = tilesM * tilesN;
+    // tiles enumerate (m tile, n tile, k split); split s covers the k-steps
+    // [s * kper, min(nkt, (s + 1) * kper))
+    const int nmn = tilesM * tilesN;
+    const int ntiles = nmn * ((nkt + kper - 1) / kper);
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -253,8 +273,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int g = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int m0 = (tile % tilesM) * TC_BM, n0 = (tile / tilesM) * BN;
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                const int mn = tile % nmn, ks = tile / nmn;
+                const int m0 = (mn % tilesM) * TC_BM, n0 = (mn / tilesM) * BN;
+                const int kb = ks * kper, ke = min(nkt, kb + kper);
+                for (int kt = kb; kt < ke; ++kt, ++g) {
                     const int s = g % TC_STAGES, round = g / TC_STAGES;
                     if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
                         atomicExch(err, 1);
@@ -283,7 +305,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * BN);
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                const int kb = (tile / nmn) * kper, ke = min(nkt, kb + kper);
+                for (int kt = kb; kt < ke; ++kt, ++g) {
                     const int s = g % TC_STAGES, round = g / TC_STAGES;
                     if (!mbar_wait(&full[s], round & 1)) {
                         atomicExch(err, 2);
@@ -295,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk)
                         mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                                 (kt > 0 || kk > 0) ? 1u : 0u);
+                                 (kt > kb || kk > 0) ? 1u : 0u);
                     mma_commit(&empty[s]);
                     *consumed = g + 1;
                 }
@@ -316,7 +339,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int j = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
             const int buf = j & 1, u = j >> 1;
-            const int m0 = (tile % tilesM) * TC_BM, n0 = (tile / tilesM) * BN;
+            const int mn = tile % nmn, ksp = tile / nmn;
+            const int m0 = (mn % tilesM) * TC_BM, n0 = (mn / tilesM) * BN;
             const bool ok = mbar_wait(&accf[buf], u & 1);
             tc_fence_after();
             if (!ok) {
@@ -324,7 +348,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
-            if (epi.mode == 2) {
+            if (epi.mode == 5) {
+                // split-K partial: ws[(split * N + n) * M + m], lanes along m
+                const long m = (long)m0 + 32 * q + lane;
+                float* ws = epi.C32 + (long)ksp * epi.N * epi.M + m;
+#pragma unroll 1
+                for (int ch = ch0; ch < ch1; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+                    if (m >= epi.M) continue;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const long nn = (long)n0 + ch * 32 + jj;
+                        if (nn < epi.N) ws[nn * epi.M] = __uint_as_float(r[jj]);
+                    }
+                }
+            } else if (epi.mode == 2) {
                 // lane = row; BF16 conversion staged through shared memory, then
                 // each row's 64 contiguous bytes go out as four 16-byte vectors,
                 // 8 rows per warp instruction
@@ -403,78 +442,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const bool rowok = m < epi.M;
                 const long roff = !rowok ? 0 : epi.mrow ? epi.mrow[m] : decomp1(m, epi.nm, epi.m_size, epi.m_s);
                 const float alpha = (float)epi.alpha;
+                // offsets in C of this warp's columns, once per tile, kept in
+                // the warp's staging slot (-1: column outside C)
+                long* coffs = (long*)(staging + (warp - 2) * 32 * 64 * 2);
+                for (int cc = lane; cc < (ch1 - ch0) * 32; cc += 32) {
+                    const long nidx = (long)n0 + ch0 * 32 + cc;
+                    coffs[cc] = nidx < epi.N ? decomp1_u32((unsigned)nidx, epi.nn, epi.n_size, epi.n_s) : -1;
+                }
+                __syncwarp();
 #pragma unroll 1
                 for (int ch = ch0; ch < ch1; ++ch) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)(ch * 32), r);
                     if (!rowok) continue;
-                    // column offsets: decompose the chunk's first column once,
-                    // then step the mode counters (no divisions per element)
-                    long ci[kMaxMode];
-                    long coff = 0;
-                    {
-                        long idx = (long)n0 + ch * 32;
-#pragma unroll
-                        for (int k = kMaxMode - 1; k >= 0; --k) {
-                            if (k < epi.nn) {
-                                const long qq = idx / epi.n_size[k];
-                                ci[k] = idx - qq * epi.n_size[k];
-                                coff += ci[k] * epi.n_s[k];
-                                idx = qq;
-                            } else {
-                                ci[k] = 0;
-                            }
-                        }
-                    }
-                    // two halves of 16 columns (keeps the offset and old-value
-                    // arrays in registers)
+                    const long* cb = coffs + (ch - ch0) * 32;
+                    // two halves of 16 columns: all loads of a half, then its stores
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        long offs[16];
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            offs[jj] = ((long)n0 + ch * 32 + h * 16 + jj < epi.N) ? roff + coff : -1;
-#pragma unroll
-                            for (int k = kMaxMode - 1; k >= 0; --k) {
-                                if (k < epi.nn) {
-                                    coff += epi.n_s[k];
-                                    if (++ci[k] < epi.n_size[k]) break;
-                                    coff -= ci[k] * epi.n_s[k];
-                                    ci[k] = 0;
-                                }
-                            }
-                        }
                         if (epi.mode == 4) {
                             float oldf[16];
 #pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) oldf[jj] = offs[jj] >= 0 ? epi.C32[offs[jj]] : 0.0f;
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj)
-                                if (offs[jj] >= 0) epi.C32[offs[jj]] = fmaf(alpha, __uint_as_float(r[h * 16 + jj]), oldf[jj]);
-                        } else if (epi.mode == 0) {
-                            // all loads of the half first, then the stores
-                            double old[16];
-                            if (epi.beta != 0.0) {
-#pragma unroll
-                                for (int jj = 0; jj < 16; ++jj) old[jj] = offs[jj] >= 0 ? epi.C[offs[jj]] : 0.0;
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const long co = cb[h * 16 + jj];
+                                oldf[jj] = co >= 0 ? epi.C32[roff + co] : 0.0f;
                             }
 #pragma unroll
                             for (int jj = 0; jj < 16; ++jj) {
-                                if (offs[jj] < 0) continue;
-                                const double v = (double)(alpha * __uint_as_float(r[h * 16 + jj]));
-                                epi.C[offs[jj]] = epi.beta != 0.0 ? fma(epi.beta, old[jj], v) : v;
+                                const long co = cb[h * 16 + jj];
+                                if (co >= 0) epi.C32[roff + co] = fmaf(alpha, __uint_as_float(r[h * 16 + jj]), oldf[jj]);
+                            }
+                        } else if (epi.mode == 0) {
+                            double old[16];
+                            if (epi.beta != 0.0) {
+#pragma unroll
+                                for (int jj = 0; jj < 16; ++jj) {
+                                    const long co = cb[h * 16 + jj];
+                                    old[jj] = co >= 0 ? epi.C[roff + co] : 0.0;
+                                }
+                            }
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const long co = cb[h * 16 + jj];
+                                if (co < 0) continue;
+                                const double v = f32_to_f64(alpha * __uint_as_float(r[h * 16 + jj]));
+                                epi.C[roff + co] = epi.beta != 0.0 ? fma(epi.beta, old[jj], v) : v;
                             }
                         } else {
 #pragma unroll
                             for (int jj = 0; jj < 16; ++jj) {
-                                if (offs[jj] < 0) continue;
+                                const long co = cb[h * 16 + jj];
+                                if (co < 0) continue;
                                 const float v = alpha * __uint_as_float(r[h * 16 + jj]);
                                 for (int sgm = 0; sgm < epi.nseg; ++sgm)
-                                    epi.P[offs[jj] + sgm * epi.segstride] = split_part(v, epi.pat[sgm]);
+                                    epi.P[roff + co + sgm * epi.segstride] = split_part(v, epi.pat[sgm]);
                             }
                         }
                     }
                 }
+                __syncwarp();  // the next tile rewrites coffs
             }
             tc_fence_before();
             __syncwarp();
@@ -506,67 +531,58 @@ struct PackArgs {
     const long* rtab;     // if set: row -> source offset (replaces the row modes)
 };
 
-// offset of a linear index over up to kMaxMode modes (last mode fastest);
-// indices and mode sizes are below 2^31, so the divisions are 32-bit
-__device__ __forceinline__ long decomp1_u32(unsigned idx, int nmode, const long* size, const long* s) {
-    long o = 0;
-#pragma unroll
-    for (int j = kMaxMode - 1; j >= 0; --j) {
-        if (j < nmode) {
-            const unsigned sz = (unsigned)size[j];
-            const unsigned q = idx / sz;
-            o += (long)(idx - q * sz) * s[j];
-            idx = q;
-        }
-    }
-    return o;
-}
-
-// 64 rows x 64 k per tile: coalesced FP64 reads (along whichever of row or k
-// is contiguous in the source), conversion to FP32 in shared memory, then
-// 16-byte stores of 8 BF16 values per segment.
+// TR rows x TK k per tile (TR * TK = 4096): coalesced FP64 reads along
+// whichever of row or k is contiguous in the source, conversion to FP32 in
+// shared memory, then 16-byte stores of 8 BF16 values per segment.
+template <int TR, int TK>
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
-    __shared__ float tile[64][65];
-    __shared__ long roff[64], koff[64];
-    const long ntr = (a.rows + 63) / 64, ntk = (a.Kp + 63) / 64;
+    __shared__ float tile[TR][TK + 1];
+    __shared__ long roff[TR], koff[TK];
+    const long ntr = (a.rows + TR - 1) / TR, ntk = (a.Kp + TK - 1) / TK;
     const long ldd = (long)a.nseg * a.Kp;
     for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
-        const long r0 = (t / ntk) * 64, k0 = (t % ntk) * 64;
+        // consecutive tiles: along k for k-contiguous sources, along the rows
+        // otherwise, so that the blocks in flight read nearby addresses (for
+        // row-contiguous sources the k planes can be megabytes apart)
+        const long r0 = (a.kfast ? t / ntk : t % ntr) * TR, k0 = (a.kfast ? t % ntk : t / ntr) * TK;
         // source offsets of the tile's rows and columns (-1: reads as zero)
-        if (threadIdx.x < 64) {
-            const long r = r0 + threadIdx.x;
-            long o = -1;
-            if (r < a.rows) {
-                const unsigned ru = (unsigned)r;
-                if (a.rtab) o = a.rtab[r];
-                else if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
-                    o = decomp1_u32(ru, a.nr, a.r_size, a.r_s);
+        for (int x = threadIdx.x; x < TR + TK; x += blockDim.x) {
+            if (x < TR) {
+                const long r = r0 + x;
+                long o = -1;
+                if (r < a.rows) {
+                    const unsigned ru = (unsigned)r;
+                    if (a.rtab) o = a.rtab[r];
+                    else if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
+                        o = decomp1_u32(ru, a.nr, a.r_size, a.r_s);
+                }
+                roff[x] = o;
+            } else {
+                const int kk = x - TR;
+                const long k = k0 + kk;
+                long o = -1;
+                if (k < a.K) {
+                    const unsigned ku = (unsigned)k;
+                    if (a.nk == 0 || (long)(ku % (unsigned)a.k_size[a.nk - 1]) < a.kvalid)
+                        o = decomp1_u32(ku, a.nk, a.k_size, a.k_s);
+                }
+                koff[kk] = o;
             }
-            roff[threadIdx.x] = o;
-        } else if (threadIdx.x < 128) {
-            const int kk = threadIdx.x - 64;
-            const long k = k0 + kk;
-            long o = -1;
-            if (k < a.K) {
-                const unsigned ku = (unsigned)k;
-                if (a.nk == 0 || (long)(ku % (unsigned)a.k_size[a.nk - 1]) < a.kvalid)
-                    o = decomp1_u32(ku, a.nk, a.k_size, a.k_s);
-            }
-            koff[kk] = o;
         }
         __syncthreads();
 #pragma unroll 4
-        for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        for (int e = threadIdx.x; e < TR * TK; e += 256) {
             int rr, kk;
-            if (a.kfast) { kk = e & 63; rr = e >> 6; }
-            else { rr = e & 63; kk = e >> 6; }
+            if (a.kfast) { kk = e % TK; rr = e / TK; }
+            else { rr = e % TR; kk = e / TR; }
             const long ro = roff[rr], ko = koff[kk];
             tile[rr][kk] = (ro >= 0 && ko >= 0) ? f64_to_f32(a.src[ro + ko]) : 0.0f;
         }
         __syncthreads();
-        // 64 rows x 8 groups of 8 k: 8 consecutive threads cover one row
-        for (int it = threadIdx.x; it < 64 * 8; it += 256) {
-            const int g = it & 7, rr = it >> 3;
+        // TR rows x TK/8 groups of 8 k
+        constexpr int G = TK / 8;
+        for (int it = threadIdx.x; it < TR * G; it += 256) {
+            const int g = it % G, rr = it / G;
             const long r = r0 + rr;
             if (r >= a.rows) continue;
             float v[8];
@@ -604,6 +620,8 @@ struct TcEngine {
     long* d_pairoff = nullptr;  // [2P] t2 offset of the same-spin pair rows
     int* d_rowcode = nullptr;   // [rows] block/i/j code of every row
     long* d_growoff = nullptr;  // [rows] offset of the row's G[blk][i][j] slice
+    float* wsk = nullptr;       // split-K partial tiles
+    size_t wsk_cap = 0;
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -645,6 +663,7 @@ void tc_free(Ctx* c) {
     if (e->d_pairoff) cudaFree(e->d_pairoff);
     if (e->d_rowcode) cudaFree(e->d_rowcode);
     if (e->d_growoff) cudaFree(e->d_growoff);
+    if (e->wsk) cudaFree(e->wsk);
     delete e;
     c->tc = nullptr;
 }
@@ -695,13 +714,18 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
         c->err = "pack: K padding must be a multiple of 64 and sizes below 2^31";
         return DCSD_ERR_INVALID_ARG;
     }
-    long tiles = ((rows + 63) / 64) * (Kp / 64);
+    const int TR = 64, TK = 64;
+    long tiles = ((rows + TR - 1) / TR) * (Kp / TK);
     unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, (long)c->num_sms * 8));
     prof_begin(c, DCSD_PROF_PACK);
-    if (c->trace)
-        trace_begin(c, "pack " + c->cur_spec + " rows=" + std::to_string(rows) + " K=" + std::to_string(K) + " kfast=" +
-                           std::to_string(a.kfast));
-    k_pack<<<g, 256, 0, c->stream>>>(a);
+    if (c->trace) {
+        const std::string label = "pack " + c->cur_spec + " rows=" + std::to_string(rows) + " K=" + std::to_string(K) +
+                                  " kfast=" + std::to_string(a.kfast);
+        if (c->trace_seq) fprintf(stderr, "[dcsd pack #%d] %s\n", c->pack_seq, label.c_str());
+        trace_begin(c, label);
+    }
+    ++c->pack_seq;
+    k_pack<64, 64><<<g, 256, 0, c->stream>>>(a);
     trace_end(c);
     prof_end(c, DCSD_PROF_PACK);
     return launch_check(c, "tc_pack");
@@ -709,7 +733,7 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
 
 // C = alpha * A_p B_p^T (+ beta C); A_p [M][Ktot], B_p [N][Ktot] packed BF16
 static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __nv_bfloat16* Bp, long N,
-                               long Ktot, TcEpi& epi) {
+                               long Ktot, TcEpi& epi, int ksplit = 1) {
     TcEngine* e = c->tc;
     if (!e->attr_set) {
         size_t s256 = TC_STAGES * (TC_BM * TC_BK * 2 + 256 * TC_BK * 2) + kStageBytesMode2 + 2048;
@@ -726,11 +750,18 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     epi.N = N;
     const int nkt = (int)(Ktot / TC_BK);
     const long tilesM = (M + TC_BM - 1) / TC_BM, tilesN = (N + BN - 1) / BN;
-    if (tilesM * tilesN > (1l << 31) - 1) {
+    if (tilesM * tilesN > (1l << 31) - 1 || M >= (1l << 31) || N >= (1l << 31)) {
         c->err = "tensor-core GEMM too large";
         return DCSD_ERR_INVALID_ARG;
     }
-    dim3 grid((unsigned)std::min<long>(tilesM * tilesN, c->num_sms));
+    ksplit = std::max(1, std::min(ksplit, nkt));
+    const int kper = (nkt + ksplit - 1) / ksplit;
+    const long ntiles = tilesM * tilesN * ((nkt + kper - 1) / kper);
+    if (ntiles > (1l << 31) - 1) {
+        c->err = "tensor-core GEMM too large";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    dim3 grid((unsigned)std::min<long>(ntiles, c->num_sms));
     size_t smem = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
     const int cls = c->ladder_phase ? DCSD_PROF_LADDER : DCSD_PROF_TC_OTHER;
     prof_begin(c, cls);
@@ -743,9 +774,9 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     }
     ++c->tc_seq;
     if (BN == 256)
-        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, e->d_err);
     else
-        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, e->d_err);
+        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, e->d_err);
     trace_end(c);
     prof_end(c, cls);
     return launch_check(c, "tc_gemm");
@@ -772,6 +803,24 @@ static void split_patterns(int nsplit, int& nseg, int* pa, int* pb) {
     }
 }
 
+// C[m,n] = alpha * sum_s ws[(s * N + n) * M + m] (+ beta * C), or the FP32
+// shadow += alpha * sum (mode 4), with the offsets of the epilogue's modes
+__global__ void k_tc_splitk_reduce(TcEpi epi, int ksplit, const float* ws) {
+    const long MN = epi.M * epi.N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < MN; e += (long)gridDim.x * blockDim.x) {
+        const long n = e / epi.M, m = e - n * epi.M;
+        double v = 0.0;
+        for (int s = 0; s < ksplit; ++s) v += (double)ws[(long)s * MN + e];
+        const long off = decomp1(m, epi.nm, epi.m_size, epi.m_s) + decomp1(n, epi.nn, epi.n_size, epi.n_s);
+        if (epi.mode == 4) {
+            epi.C32[off] += (float)(epi.alpha * v);
+        } else {
+            const double r = epi.alpha * v;
+            epi.C[off] = epi.beta != 0.0 ? fma(epi.beta, epi.C[off], r) : r;
+        }
+    }
+}
+
 dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
                       const TV& C, int nsplit) {
     c->cur_spec = spec;
@@ -788,12 +837,31 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         c->err = err;
         return DCSD_ERR_INVALID_ARG;
     }
-    if (p.NB != 1 || p.M < 1 || p.N < 1 || p.K < 16) return einsum64(c, spec, alpha, A, B, beta, C);
+    // batched or very short contractions: FP32 products on the CUDA cores
+    if (p.NB != 1 || p.M < 1 || p.N < 1 || p.K < 16) return einsum32(c, spec, alpha, A, B, beta, C);
     TcEngine* e = c->tc;
     int nseg, pa[6], pb[6];
     split_patterns(nsplit, nseg, pa, pb);
     const long Kp = round_up(p.K, TC_BK);
     const long Kt = nseg * Kp;
+    // A long contraction onto few output tiles splits K over the SMs
+    // (FP32 partial tiles, summed by a second kernel).  Rough time model:
+    // 0.4 us per 64-deep k-step and tile wave plus operand packing at
+    // 3 TB/s, against 5 TFLOP/s of the FP32 CUDA-core kernel on its 64 x 64
+    // tiles; the faster one runs.
+    int ksplit = 1;
+    {
+        const long nkt = Kt / TC_BK;
+        const long bn = p.N >= 256 ? 256 : 128;
+        const long tilesMN = ((p.M + TC_BM - 1) / TC_BM) * ((p.N + bn - 1) / bn);
+        if (tilesMN <= c->num_sms / 2 && nkt >= 64)
+            ksplit = (int)std::max<long>(1, std::min<long>(c->num_sms / tilesMN, nkt / 16));
+        const long kper = (nkt + ksplit - 1) / ksplit;
+        const long waves = (tilesMN * ksplit + c->num_sms - 1) / std::max(1, c->num_sms);
+        const double tc_us = (double)waves * (double)kper * 0.4 + (double)(p.M + p.N) * (double)p.K * 8.0 / 3e6;
+        const double simt_us = 2.0 * (double)round_up(p.M, 64) * (double)round_up(p.N, 64) * (double)p.K / 5e6;
+        if (simt_us < tc_us) return einsum32(c, spec, alpha, A, B, beta, C);
+    }
     // Row order within M (and N) is free: the packed operand and the
     // epilogue only have to agree.  Order each side's modes by decreasing
     // stride in C, so that its fastest mode is the one closest to C's
@@ -851,7 +919,31 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         epi.n_size[i] = i < p.nn ? p.n_size[i] : 1;
         epi.n_s[i] = i < p.nn ? p.n_sc[i] : 0;
     }
-    return gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi);
+    if (ksplit <= 1) return gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi);
+    // split K: partial tiles, then C (or its FP32 shadow) from their sum
+    {
+        const int nkt = (int)(Kt / TC_BK), kper = (nkt + ksplit - 1) / ksplit;
+        ksplit = (nkt + kper - 1) / kper;
+    }
+    const size_t wsn = (size_t)ksplit * p.M * p.N;
+    if (e->wsk_cap < wsn) {
+        if (e->wsk) cudaFree(e->wsk);
+        e->wsk = nullptr;
+        e->wsk_cap = 0;
+        DCSD_CUDA(c, cudaMalloc((void**)&e->wsk, wsn * sizeof(float)));
+        e->wsk_cap = wsn;
+    }
+    TcEpi red = epi;
+    red.M = p.M;
+    red.N = p.N;
+    epi.mode = 5;
+    epi.C32 = e->wsk;
+    DCSD_TRY(gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi, ksplit));
+    if (c->trace) trace_begin(c, "tc-splitk-reduce " + c->cur_spec);
+    k_tc_splitk_reduce<<<(unsigned)std::max<long>(1, std::min<long>((p.M * p.N + 255) / 256, (long)c->num_sms * 8)),
+                         256, 0, c->stream>>>(red, ksplit, e->wsk);
+    trace_end(c);
+    return launch_check(c, "tc_splitk_reduce");
 }
 
 // ---------------------------------------------------------------------------

@@ -96,7 +96,9 @@ def test_invalid_arguments_rejected(P):
 # the largest contributing products, observed <= 5e-3 max|R|: tolerance 2e-2
 # max|R|.  The split (hi+lo) products carry 2^-17 relative error per product;
 # FP32 accumulation then dominates: tolerance 2e-4 max|R|.
-@pytest.mark.parametrize("dims,seed", [((2, 5, 12), 3), ((4, 20, 30), 4), ((6, 40, 64), 5)])
+# (4, 60, 200): long DF contractions onto few output tiles take the split-K
+# tensor-core path
+@pytest.mark.parametrize("dims,seed", [((2, 5, 12), 3), ((4, 20, 30), 4), ((6, 40, 64), 5), ((4, 60, 200), 6)])
 @pytest.mark.parametrize("prec,rtol", [(1, 2e-2), (2, 2e-4), (4, 2e-5)])
 @pytest.mark.parametrize("method", [0, 1])
 def test_residual_tensor_core_within_precision(P, dims, seed, prec, rtol, method):
