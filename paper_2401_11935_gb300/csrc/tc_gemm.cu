@@ -529,6 +529,11 @@ struct PackArgs {
     int kfast;  // source contiguous along k
     long rvalid, kvalid;  // innermost row / k mode indices >= these read as 0
     const long* rtab;     // if set: row -> source offset (replaces the row modes)
+    // Row modes are listed in the order tiles enumerate them (last fastest);
+    // r_d is each mode's stride in the packed row index and rv_pos the mode
+    // that rvalid applies to.
+    long r_d[kMaxMode];
+    int rv_pos;
 };
 
 // TR rows x TK k per tile (TR * TK = 4096): coalesced FP64 reads along
@@ -537,7 +542,7 @@ struct PackArgs {
 template <int TR, int TK>
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
     __shared__ float tile[TR][TK + 1];
-    __shared__ long roff[TR], koff[TK];
+    __shared__ long roff[TR], rdst[TR], koff[TK];
     const long ntr = (a.rows + TR - 1) / TR, ntk = (a.Kp + TK - 1) / TK;
     const long ldd = (long)a.nseg * a.Kp;
     for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
@@ -549,14 +554,32 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
         for (int x = threadIdx.x; x < TR + TK; x += blockDim.x) {
             if (x < TR) {
                 const long r = r0 + x;
-                long o = -1;
+                long o = -1, d = -1;
                 if (r < a.rows) {
-                    const unsigned ru = (unsigned)r;
-                    if (a.rtab) o = a.rtab[r];
-                    else if (a.nr == 0 || (long)(ru % (unsigned)a.r_size[a.nr - 1]) < a.rvalid)
-                        o = decomp1_u32(ru, a.nr, a.r_size, a.r_s);
+                    if (a.rtab) {
+                        o = a.rtab[r];
+                        d = r;
+                    } else {
+                        unsigned u = (unsigned)r;
+                        long so = 0, dr = 0;
+                        bool ok = true;
+#pragma unroll
+                        for (int j = kMaxMode - 1; j >= 0; --j) {
+                            if (j < a.nr) {
+                                const unsigned sz = (unsigned)a.r_size[j];
+                                const unsigned qq = u / sz, ix = u - qq * sz;
+                                so += (long)ix * a.r_s[j];
+                                dr += (long)ix * a.r_d[j];
+                                if (j == a.rv_pos && (long)ix >= a.rvalid) ok = false;
+                                u = qq;
+                            }
+                        }
+                        d = dr;
+                        if (ok) o = so;
+                    }
                 }
                 roff[x] = o;
+                rdst[x] = d;
             } else {
                 const int kk = x - TR;
                 const long k = k0 + kk;
@@ -583,8 +606,8 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
         constexpr int G = TK / 8;
         for (int it = threadIdx.x; it < TR * G; it += 256) {
             const int g = it % G, rr = it / G;
-            const long r = r0 + rr;
-            if (r >= a.rows) continue;
+            const long r = rdst[rr];
+            if (r < 0) continue;
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = tile[rr][g * 8 + q];
@@ -703,13 +726,36 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
     for (int i = 0; i < 6; ++i) a.pat[i] = i < nseg ? pat[i] : 0;
     a.nr = nr;
     a.nk = nk;
+    a.kfast = (nk > 0 && ks[nk - 1] == 1) ? 1 : 0;
+    // enumeration order of the row modes: the packed order, except that a
+    // source that is contiguous along a slower row mode (and not along k)
+    // has that mode enumerated fastest, so each tile reads contiguous runs
+    int order[kMaxMode];
+    for (int i = 0; i < nr; ++i) order[i] = i;
+    if (!rtab && !a.kfast && nr >= 2) {
+        int js = -1;
+        for (int i = 0; i < nr; ++i)
+            if (std::labs(rs[i]) == 1 && rsz[i] > 1) js = i;
+        if (js >= 0 && js != nr - 1) {
+            for (int i = js; i < nr - 1; ++i) order[i] = order[i + 1];
+            order[nr - 1] = js;
+        }
+    }
+    long dstr[kMaxMode];
+    long st = 1;
+    for (int i = nr - 1; i >= 0; --i) {
+        dstr[i] = st;
+        st *= rsz[i];
+    }
+    a.rv_pos = -1;
     for (int i = 0; i < kMaxMode; ++i) {
-        a.r_size[i] = i < nr ? rsz[i] : 1;
-        a.r_s[i] = i < nr ? rs[i] : 0;
+        a.r_size[i] = i < nr ? rsz[order[i]] : 1;
+        a.r_s[i] = i < nr ? rs[order[i]] : 0;
+        a.r_d[i] = i < nr ? dstr[order[i]] : 0;
+        if (i < nr && order[i] == nr - 1) a.rv_pos = i;
         a.k_size[i] = i < nk ? ksz[i] : 1;
         a.k_s[i] = i < nk ? ks[i] : 0;
     }
-    a.kfast = (nk > 0 && ks[nk - 1] == 1) ? 1 : 0;
     if (Kp % 64 != 0 || rows >= (1l << 31) || Kp >= (1l << 31)) {
         c->err = "pack: K padding must be a multiple of 64 and sizes below 2^31";
         return DCSD_ERR_INVALID_ARG;
@@ -987,8 +1033,11 @@ static std::vector<std::pair<long, long>> ladder_chunks(long V, long Vp, long ro
     std::vector<long> pick(V + 1, 1);
     for (long r0 = V - 1; r0 >= 0; --r0) {
         best[r0] = 1e300;
-        for (long nr = 1; nr <= std::min(nmax, V - r0); ++nr) {
-            const long Vb = V - r0;
+        const long Vb = V - r0;
+        // the V tile holds nmax * V rows (r, b); near the end of the triangle
+        // (small Vb) more rows r fit, up to the producer A buffer's 4 * nmax
+        const long cap = std::min(4 * nmax, std::max(nmax, nmax * V / std::max<long>(1, Vb)));
+        for (long nr = 1; nr <= std::min(cap, V - r0); ++nr) {
             const double cost = (double)waves(rows, nr * Vb) * (double)(K2t / TC_BK) +
                                 (double)waves(nr * V, Vb * Vp) * (double)(Xt / TC_BK) + launch + best[r0 + nr];
             if (cost < best[r0]) {
@@ -1074,7 +1123,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     }
     const long chunk = std::max<long>(1, std::min<long>(V, 16));
     DCSD_TRY(ensure(c, e->pv, (size_t)chunk * V * K2t));
-    DCSD_TRY(ensure(c, e->pa, (size_t)chunk * V * Xt));
+    DCSD_TRY(ensure(c, e->pa, (size_t)4 * chunk * V * Xt));
     struct PhaseGuard {
         Ctx* c;
         ~PhaseGuard() { c->ladder_phase = 0; c->cur_spec = ""; }
