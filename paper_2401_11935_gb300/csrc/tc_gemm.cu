@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -224,12 +225,23 @@ constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kStageBytesMode2 = kEpiWarps * 32 * 64 * 2;  // epilogue staging, per warp 2 halves x 32 rows x 64 B
 
 // Persistent tcgen05 GEMM: one CTA per SM walks the output tiles (m fastest);
+// Output tile of a linear (m, n) tile index in grouped order: bands of
+// `group` m-tiles, n-tiles running within a band, so that the CTAs of one
+// wave share a compact block of A rows and B rows in L2.
+__device__ __forceinline__ void tile_mn(int mn, int tilesM, int tilesN, int group, int& tm, int& tn) {
+    const int g = max(1, min(group, tilesM));
+    const int band = mn / (g * tilesN), r = mn - band * g * tilesN;
+    const int rows = min(g, tilesM - band * g);
+    tm = band * g + r % rows;
+    tn = r / rows;
+}
+
 // two TMEM accumulators of BN columns let the epilogue of one tile overlap
 // the MMAs of the next.
 template <int BN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
-              int nkt, int tilesM, int tilesN, int kper, int* err) {
+              int nkt, int tilesM, int tilesN, int kper, int group, int* err) {
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
     constexpr uint32_t STAGE = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
@@ -274,7 +286,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int mn = tile % nmn, ks = tile / nmn;
-                const int m0 = (mn % tilesM) * TC_BM, n0 = (mn / tilesM) * BN;
+                int tm, tn;
+                tile_mn(mn, tilesM, tilesN, group, tm, tn);
+                const int m0 = tm * TC_BM, n0 = tn * BN;
                 const int kb = ks * kper, ke = min(nkt, kb + kper);
                 for (int kt = kb; kt < ke; ++kt, ++g) {
                     const int s = g % TC_STAGES, round = g / TC_STAGES;
@@ -340,7 +354,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
             const int buf = j & 1, u = j >> 1;
             const int mn = tile % nmn, ksp = tile / nmn;
-            const int m0 = (mn % tilesM) * TC_BM, n0 = (mn / tilesM) * BN;
+            int tm, tn;
+            tile_mn(mn, tilesM, tilesN, group, tm, tn);
+            const int m0 = tm * TC_BM, n0 = tn * BN;
             const bool ok = mbar_wait(&accf[buf], u & 1);
             tc_fence_after();
             if (!ok) {
@@ -808,6 +824,16 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
         return DCSD_ERR_INVALID_ARG;
     }
     dim3 grid((unsigned)std::min<long>(ntiles, c->num_sms));
+    // m-tile band height that minimises the A and B rows one wave of
+    // num_sms tiles touches: g * BM + (num_sms / g) * BN
+    // (an operand that fits in a quarter of L2 is kept there instead: all
+    // m-tiles of a band when A fits, one m-tile per band when B fits)
+    int group = (int)std::lround(std::sqrt((double)c->num_sms * BN / TC_BM));
+    const double l2q = 32e6;
+    // (the ladder's long-K contractions measured best with all m-tiles per band)
+    if ((double)M * (double)Ktot * 2.0 <= l2q || c->ladder_phase) group = (int)tilesM;
+    else if ((double)N * (double)Ktot * 2.0 <= l2q) group = 1;
+    group = (int)std::max<long>(1, std::min<long>(group, tilesM));
     size_t smem = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
     const int cls = c->ladder_phase ? DCSD_PROF_LADDER : DCSD_PROF_TC_OTHER;
     prof_begin(c, cls);
@@ -820,9 +846,9 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     }
     ++c->tc_seq;
     if (BN == 256)
-        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, e->d_err);
+        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group, e->d_err);
     else
-        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, e->d_err);
+        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group, e->d_err);
     trace_end(c);
     prof_end(c, cls);
     return launch_check(c, "tc_gemm");
