@@ -68,7 +68,7 @@ typedef enum {
     DCSD_PREC_FP64 = 0,   /* FP64 on CUDA cores                              */
     DCSD_PREC_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 acc */
     DCSD_PREC_BF16X3 = 2, /* split operands hi+mid, 3 BF16 products          */
-    DCSD_PREC_MIXED = 3,  /* dcsd_solve only: BF16, then BF16X6 (see below)  */
+    DCSD_PREC_MIXED = 3,  /* dcsd_solve only: BF16, BF16X6, FP64 (see below) */
     DCSD_PREC_BF16X6 = 4  /* split hi+mid+lo, 6 BF16 products (FP32-class)  */
 } dcsd_precision;
 
@@ -90,6 +90,14 @@ typedef struct {
     double switch_tol;  /* MIXED: switch BF16 -> BF16X6 when max|R| < this, or
                            when max|R| has not halved in 6 iterations      */
     int use_guess;      /* 1: start from the T passed in, 0: from T = 0      */
+    double polish_tol;  /* MIXED: switch BF16X6 -> FP64 when max|R| < this, or
+                           when max|R| has not halved in 4 BF16X6 iterations;
+                           0 keeps BF16X6 to the end.  The tensor cores
+                           accumulate in FP32, whose rounding noise in long
+                           contractions puts a floor under the attainable
+                           accuracy of the energies; the FP64 iterations
+                           remove it (the converged T then solves the FP64
+                           equations) */
 } dcsd_solve_opts;
 
 typedef struct {
@@ -101,7 +109,8 @@ typedef struct {
     int iters;        /* residual evaluations performed                     */
     int converged;    /* 1 if max_r <= tol                                   */
     double seconds;   /* wall time of the solve                             */
-    int switched_at;  /* MIXED: iteration of the precision switch, or -1    */
+    int switched_at;  /* MIXED: iteration of the BF16 -> BF16X6 switch, or -1 */
+    int polished_at;  /* MIXED: iteration of the BF16X6 -> FP64 switch, or -1 */
 } dcsd_result;
 
 /* dcsd_init -- create a context (Section II inputs of the method).
@@ -200,6 +209,72 @@ typedef enum {
  * Errors: INVALID_ARG (NULL ctx), CUDA. */
 dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
                          long long* launches);
+
+/* dcsd_vjp -- vector-Jacobian product of the FP64 residual (reverse mode).
+ * For the residual R(T) of dcsd_residual (same ref, method) with outputs
+ * (R1a, R1b, R2aa, R2bb, R2ab, dE_A, W), returns for given cotangents
+ * (R_bar, dEA_bar, W_bar) the gradients of
+ *     <R_bar, R(T)> + dEA_bar * dE_A(T) + W_bar * W(T)
+ * with respect to the stored amplitude arrays (every element, as stored;
+ * T2aa and T2bb are read as full arrays), the DF factors B and the two Fock
+ * matrices of dcsd_init.  The paper has no counterpart; this is the
+ * derivative of the Section II residual used for the Lambda equations and
+ * the response density of dcsd_lambda.
+ *   T1a .. T2ab       : amplitudes, layout of this header.
+ *   R1a_bar .. R2ab_bar : residual cotangents, same layouts; all five NULL
+ *                       means zero.
+ *   dEA_bar, W_bar    : cotangents of dE_A and W.
+ *   T1a_bar .. T2ab_bar : out, gradients, same layouts.
+ *   B_bar             : out or NULL, [naux][n][n] (both triangles: the
+ *                       gradient with respect to the array as stored).
+ *   fock_a_bar, fock_b_bar : out or NULL, [n][n].
+ * Pointers are host or device memory according to mem_kind.  The call runs
+ * the FP64 residual once while recording its operations and then their
+ * adjoints; the particle-particle ladder integrals are rebuilt in the
+ * reverse sweep, not stored.  Other intermediates are kept in device memory
+ * for the duration of the call (about 25 doubly-sized amplitude arrays).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+dcsd_status dcsd_vjp(dcsd_ctx* ctx, int ref, int method, int mem_kind,
+                     const double* T1a, const double* T1b, const double* T2aa,
+                     const double* T2bb, const double* T2ab,
+                     const double* R1a_bar, const double* R1b_bar, const double* R2aa_bar,
+                     const double* R2bb_bar, const double* R2ab_bar,
+                     double dEA_bar, double W_bar,
+                     double* T1a_bar, double* T1b_bar, double* T2aa_bar,
+                     double* T2bb_bar, double* T2ab_bar,
+                     double* B_bar, double* fock_a_bar, double* fock_b_bar);
+
+/* dcsd_lambda -- Lambda equations and response density of one state.
+ * With E = dE_A + state * W (state +1: the singlet of dcsd_heff's phase
+ * convention, -1: the triplet) and the Lagrangian
+ *     L(T, Lambda) = E(T) + sum_q Lambda_q R_q(T)
+ * over the residual elements of dcsd_residual, solves dL/dT = 0 for Lambda
+ * at converged amplitudes T (Jacobi steps with the amplitude denominators
+ * and DIIS; each iteration is one reverse sweep of the recorded FP64
+ * residual, see dcsd_vjp), and returns the response density
+ *     gamma^sigma_pq = dL/df^sigma_pq
+ * (the gradient with respect to the Fock matrices of dcsd_init as stored;
+ * contract its symmetric part with symmetric perturbations).  By
+ * stationarity, dE/df along any perturbation of f equals <gamma, df> once
+ * T and Lambda are converged.  The paper has no counterpart; this is the
+ * first-order property machinery of the Section II energies.
+ *   o          : method, ref, maxiter, diis_n, tol (on max |dL/dT| over the
+ *                independent amplitudes), use_guess (Lambda in L* is the
+ *                guess); precision must be DCSD_PREC_FP64.
+ *   T1a..T2ab  : converged amplitudes (dcsd_solve), layout of this header.
+ *   L1a..L2ab  : in/out Lambda, same layouts; same-spin doubles
+ *                antisymmetric, the A->B double element 0.
+ *   rdm_a, rdm_b : out or NULL, [n][n].
+ *   res        : dEA, W, E_S, E_T at T, iters, converged, max_r = final
+ *                max |dL/dT|, seconds.
+ * Pointers are host or device memory according to mem_kind.
+ * Errors: INVALID_ARG, OOM, CUDA, NUMERIC, NOT_CONVERGED (outputs hold the
+ * last iterate). */
+dcsd_status dcsd_lambda(dcsd_ctx* ctx, const dcsd_solve_opts* o, int state, int mem_kind,
+                        const double* T1a, const double* T1b, const double* T2aa,
+                        const double* T2bb, const double* T2ab,
+                        double* L1a, double* L1b, double* L2aa, double* L2bb, double* L2ab,
+                        double* rdm_a, double* rdm_b, dcsd_result* res);
 
 /* dcsd_selftest_conversions -- checks, on the current device, the FP64 <->
  * FP32 conversions that the tensor-core precision modes perform on the

@@ -88,13 +88,55 @@ class Engine:
         return L.dcsd_energy(self.ctx, ref, method, MEM_DEVICE, [_ptr(x) for x in T])
 
     def solve(self, method=DCSD, ref=0, precision=PREC_FP64, tol=1e-10, maxiter=100, diis_n=8,
-              switch_tol=1e-5, T0=None):
-        """Converge the amplitudes on the device; returns (T, dcsd_result)."""
+              switch_tol=1e-5, T0=None, polish_tol=1e-7):
+        """Converge the amplitudes on the device; returns (T, dcsd_result).
+        MIXED: BF16 until max|R| < switch_tol, BF16X6 until max|R| <
+        polish_tol, then FP64 (polish_tol = 0: no FP64 phase)."""
         T = tuple(x.clone() for x in T0) if T0 is not None else self.zeros()
         opts = L.dcsd_solve_opts(method, ref, precision, maxiter, diis_n, tol, switch_tol,
-                                 1 if T0 is not None else 0)
+                                 1 if T0 is not None else 0, polish_tol)
         res = L.dcsd_solve(self.ctx, opts, MEM_DEVICE, [_ptr(x) for x in T])
         return T, res
+
+    def vjp(self, T, Rbar=None, Ebar=0.0, Wbar=0.0, ref=0, method=DCSD, want_B=False, want_fock=False):
+        """Reverse mode of the FP64 residual (device call).  Returns the
+        gradients of <Rbar, R(T)> + Ebar * dE_A(T) + Wbar * W(T) with respect
+        to the five amplitude arrays, and optionally to the DF factors B
+        [naux, n, n] and the two Fock matrices [n, n]: (Tbar, Bbar, fa_bar,
+        fb_bar), absent ones None."""
+        t = self.torch
+        n = self.n_c + 2 + self.n_v
+        Tb = tuple(t.zeros_like(x) for x in T)
+        dev = T[0].device
+        Bb = t.zeros((self.naux, n, n), dtype=t.float64, device=dev) if want_B else None
+        Fa = t.zeros((n, n), dtype=t.float64, device=dev) if want_fock else None
+        Fb = t.zeros((n, n), dtype=t.float64, device=dev) if want_fock else None
+        L.dcsd_vjp(self.ctx, ref, method, MEM_DEVICE, [_ptr(x) for x in T],
+                   [_ptr(x) for x in Rbar] if Rbar is not None else None, Ebar, Wbar,
+                   [_ptr(x) for x in Tb], _ptr(Bb) if Bb is not None else None,
+                   _ptr(Fa) if Fa is not None else None, _ptr(Fb) if Fb is not None else None)
+        return Tb, Bb, Fa, Fb
+
+    def lambda_solve(self, T, state=1, method=DCSD, ref=0, tol=1e-9, maxiter=100, diis_n=8, L0=None,
+                     want_rdm=True):
+        """Lambda equations for E = dE_A + state * W at converged amplitudes T
+        (CUDA tensors); returns (Lambda tuple, gamma_a, gamma_b, dcsd_result)."""
+        t = self.torch
+        n = self.n_c + 2 + self.n_v
+        Lam = tuple(x.clone() for x in L0) if L0 is not None else tuple(t.zeros_like(x) for x in T)
+        ga = t.zeros((n, n), dtype=t.float64, device=T[0].device) if want_rdm else None
+        gb = t.zeros((n, n), dtype=t.float64, device=T[0].device) if want_rdm else None
+        opts = L.dcsd_solve_opts(method, ref, PREC_FP64, maxiter, diis_n, tol, 0.0, 1 if L0 is not None else 0,
+                                 0.0)
+        res = L.dcsd_lambda(self.ctx, opts, state, MEM_DEVICE, [_ptr(x) for x in T], [_ptr(x) for x in Lam],
+                            _ptr(ga) if ga is not None else None, _ptr(gb) if gb is not None else None)
+        return Lam, ga, gb, res
+
+    def residual_autograd(self, T, ref=0, method=DCSD):
+        """FP64 residual as a differentiable torch function of the amplitudes:
+        returns (R1a, R1b, R2aa, R2bb, R2ab, W, dE_A) as tensors whose
+        backward pass calls dcsd_vjp."""
+        return _residual_function().apply(self, ref, method, *T)
 
     def launches(self):
         return L.dcsd_kernel_launches(self.ctx)
@@ -109,3 +151,38 @@ class Engine:
             self.close()
         except Exception:
             pass
+
+
+_RESIDUAL_FN = None
+
+
+def _residual_function():
+    """torch.autograd.Function over the C ABI residual (built on first use so
+    that importing the package does not import torch)."""
+    global _RESIDUAL_FN
+    if _RESIDUAL_FN is not None:
+        return _RESIDUAL_FN
+    import torch
+
+    class ResidualFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, engine, ref, method, *T):
+            T = tuple(x.detach().contiguous() for x in T)
+            R, W, dE = engine.residual(T, ref=ref, method=method, precision=PREC_FP64)
+            ctx.engine, ctx.ref, ctx.method = engine, ref, method
+            ctx.save_for_backward(*T)
+            dev = T[0].device
+            return (*R, torch.tensor(W, dtype=torch.float64, device=dev),
+                    torch.tensor(dE, dtype=torch.float64, device=dev))
+
+        @staticmethod
+        def backward(ctx, *g):
+            T = ctx.saved_tensors
+            Rb = [gi.contiguous() if gi is not None else torch.zeros_like(x) for gi, x in zip(g[:5], T)]
+            Wb = float(g[5]) if g[5] is not None else 0.0
+            Eb = float(g[6]) if g[6] is not None else 0.0
+            Tb, _, _, _ = ctx.engine.vjp(T, Rbar=Rb, Ebar=Eb, Wbar=Wb, ref=ctx.ref, method=ctx.method)
+            return (None, None, None, *Tb)
+
+    _RESIDUAL_FN = ResidualFunction
+    return _RESIDUAL_FN

@@ -1,0 +1,92 @@
+"""Command-line runs of the engine on seeded synthetic inputs (for timing and
+for profiler captures of single kernels).
+
+    python -m paper_2401_11935_gb300 residual --dims 30,500,1500 --precision bf16 --repeat 1
+    python -m paper_2401_11935_gb300 solve --dims 10,120,360 --precision mixed --maxiter 40
+    python -m paper_2401_11935_gb300 compare --dims c3 --tol 1e-8
+
+compare converges the FP64 and the mixed-precision solves from the same
+guess and prints their energies (Delta E_A, W, singlet and triplet energies,
+gap 2W), the differences and the wall time of each converged solve.
+
+--dims is n_c,n_v,naux (core orbitals, external virtuals, DF functions) or
+one of the named workloads c1..c5.  The inputs come from the seeded
+generator in ``synth``; the residual is evaluated at seeded random
+amplitudes of magnitude 1e-3.  Prints one line per call with the device
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "mixed": 3, "bf16x6": 4}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_2401_11935_gb300")
+    ap.add_argument("what", choices=["residual", "solve", "compare"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--switch-tol", type=float, default=1e-5)
+    ap.add_argument("--polish-tol", type=float, default=1e-7)
+    ap.add_argument("--dims", default="c3")
+    ap.add_argument("--precision", default="bf16", choices=sorted(PREC))
+    ap.add_argument("--method", default="dcsd", choices=["ccsd", "dcsd"])
+    ap.add_argument("--ref", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--maxiter", type=int, default=60)
+    ap.add_argument("--seed", type=int, default=3)
+    a = ap.parse_args(argv)
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+    from synth import CONFIGS, make_system, random_amplitudes
+    import paper_2401_11935_gb300 as P
+
+    if a.dims in CONFIGS:
+        s = make_system(a.dims)
+    else:
+        s = make_system(tuple(int(x) for x in a.dims.split(",")), seed=a.seed)
+    method = P.DCSD if a.method == "dcsd" else P.CCSD
+    eng = P.Engine.from_system(s)
+    try:
+        if a.what == "residual":
+            Td = eng.to_device(random_amplitudes(s, seed=a.seed, ref=a.ref, scale1=1e-3, scale2=1e-3))
+            for k in range(a.repeat):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, W, dE = eng.residual(Td, ref=a.ref, method=method, precision=PREC[a.precision])
+                torch.cuda.synchronize()
+                print(f"residual {k} dims=({s.n_c},{s.n_v},{s.naux}) precision={a.precision} "
+                      f"{time.perf_counter() - t0:.4f} s  W={W:.12g} dEA={dE:.12g}", flush=True)
+        elif a.what == "solve":
+            _, res = eng.solve(ref=a.ref, method=method, precision=PREC[a.precision], maxiter=a.maxiter,
+                               tol=a.tol, switch_tol=a.switch_tol, polish_tol=a.polish_tol)
+            print(f"solve dims=({s.n_c},{s.n_v},{s.naux}) precision={a.precision} iters={res.iters} "
+                  f"converged={res.converged} switched_at={res.switched_at} polished_at={res.polished_at} "
+                  f"seconds={res.seconds:.3f} max|R|={res.max_r:.2e} dEA={res.dEA:.12f} W={res.W:.12f} "
+                  f"E_S={res.E_S:.12f} E_T={res.E_T:.12f}", flush=True)
+        else:
+            out = {}
+            for name in ("fp64", "mixed"):
+                _, res = eng.solve(ref=a.ref, method=method, precision=PREC[name], maxiter=a.maxiter,
+                                   tol=a.tol, switch_tol=a.switch_tol, polish_tol=a.polish_tol)
+                out[name] = res
+                print(f"{name:5s} iters={res.iters} converged={res.converged} switched_at={res.switched_at} "
+                      f"polished_at={res.polished_at} "
+                      f"seconds={res.seconds:.3f} max|R|={res.max_r:.2e} dEA={res.dEA:.12f} W={res.W:.12f} "
+                      f"E_S={res.E_S:.12f} E_T={res.E_T:.12f}", flush=True)
+            f, m = out["fp64"], out["mixed"]
+            print(f"mixed - fp64: dEA {m.dEA - f.dEA:+.3e}  W {m.W - f.W:+.3e}  E_S {m.E_S - f.E_S:+.3e}  "
+                  f"E_T {m.E_T - f.E_T:+.3e}  gap {2 * (m.W - f.W):+.3e} Eh;  time ratio fp64/mixed "
+                  f"{f.seconds / m.seconds:.2f}", flush=True)
+    finally:
+        eng.close()
+
+
+if __name__ == "__main__":
+    main()

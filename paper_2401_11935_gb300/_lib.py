@@ -22,7 +22,7 @@ PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
-           "dcsd_energy_noalloc", "dcsd_selftest_conversions"]
+           "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -33,13 +33,14 @@ class dcsd_dims(C.Structure):
 class dcsd_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("ref", C.c_int), ("precision", C.c_int),
                 ("maxiter", C.c_int), ("diis_n", C.c_int), ("tol", C.c_double),
-                ("switch_tol", C.c_double), ("use_guess", C.c_int)]
+                ("switch_tol", C.c_double), ("use_guess", C.c_int), ("polish_tol", C.c_double)]
 
 
 class dcsd_result(C.Structure):
     _fields_ = [("dEA", C.c_double), ("W", C.c_double), ("E_S", C.c_double),
                 ("E_T", C.c_double), ("max_r", C.c_double), ("iters", C.c_int),
-                ("converged", C.c_int), ("seconds", C.c_double), ("switched_at", C.c_int)]
+                ("converged", C.c_int), ("seconds", C.c_double), ("switched_at", C.c_int),
+                ("polished_at", C.c_int)]
 
 
 class DcsdError(RuntimeError):
@@ -75,6 +76,11 @@ def load():
     lib.dcsd_profile.restype = C.c_int
     lib.dcsd_energy_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10
     lib.dcsd_energy_noalloc.restype = C.c_int
+    lib.dcsd_vjp.argtypes = [P, C.c_int, C.c_int, C.c_int] + [P] * 10 + [C.c_double, C.c_double] + [P] * 8
+    lib.dcsd_vjp.restype = C.c_int
+    lib.dcsd_lambda.argtypes = [P, C.POINTER(dcsd_solve_opts), C.c_int, C.c_int] + [P] * 12 + \
+        [C.POINTER(dcsd_result)]
+    lib.dcsd_lambda.restype = C.c_int
     lib.dcsd_selftest_conversions.argtypes = [P, C.POINTER(C.c_longlong)]
     lib.dcsd_selftest_conversions.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
@@ -167,3 +173,19 @@ def dcsd_selftest_conversions(stream=None):
     if st != 0:
         raise DcsdError(st, "dcsd_selftest_conversions failed")
     return n.value
+
+
+def dcsd_vjp(ctx, ref, method, mem_kind, T, Rbar, Ebar, Wbar, Tbar, Bbar=None, Fa=None, Fb=None):
+    """Raw call; T, Rbar (or None), Tbar: 5 pointers each."""
+    Rb = list(Rbar) if Rbar is not None else [None] * 5
+    st = load().dcsd_vjp(ctx, ref, method, mem_kind, *T, *Rb, float(Ebar), float(Wbar), *Tbar, Bbar, Fa, Fb)
+    _check(st, ctx)
+
+
+def dcsd_lambda(ctx, opts, state, mem_kind, T, Lam, rdm_a=None, rdm_b=None):
+    """Raw call; returns the dcsd_result (raises unless converged)."""
+    res = dcsd_result()
+    st = load().dcsd_lambda(ctx, C.byref(opts), state, mem_kind, *T, *Lam, rdm_a, rdm_b, C.byref(res))
+    if st not in (0, 4):
+        _check(st, ctx)
+    return res

@@ -226,6 +226,7 @@ void free_ctx(Ctx* c) {
     }
     mtables_free(c);
     tc_free(c);
+    vjp_free(c);
 }
 
 // device ABI staging (host mem_kind)
@@ -494,13 +495,83 @@ extern "C" dcsd_status dcsd_energy(dcsd_ctx* h, int ref, int method, int mem_kin
     return residual_common(&h->c, ref, method, DCSD_PREC_FP64, mem_kind, T, nullptr, W, dEA);
 }
 
-extern "C" dcsd_status dcsd_heff(double dEA, double W, double* H, double* evals, int* singlet_index) {
-    if (!H || !evals || !singlet_index) return DCSD_ERR_INVALID_ARG;
-    H[0] = dEA; H[1] = W; H[2] = W; H[3] = dEA;
-    double lo = dEA - std::fabs(W), hi = dEA + std::fabs(W);
-    evals[0] = lo;
-    evals[1] = hi;
-    *singlet_index = W >= 0.0 ? 1 : 0;  // the singlet is dEA + W
+namespace dcsd {
+dcsd_status vjp_run(Ctx* c, int ref, int method, const double* const* Td, const double* const* Rb, double Ebar,
+                    double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb);
+}
+
+extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int mem_kind, const double* T1a,
+                                const double* T1b, const double* T2aa, const double* T2bb, const double* T2ab,
+                                const double* R1a_bar, const double* R1b_bar, const double* R2aa_bar,
+                                const double* R2bb_bar, const double* R2ab_bar, double dEA_bar, double W_bar,
+                                double* T1a_bar, double* T1b_bar, double* T2aa_bar, double* T2bb_bar,
+                                double* T2ab_bar, double* B_bar, double* fock_a_bar, double* fock_b_bar) {
+    if (!h) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
+    const double* Rb[5] = {R1a_bar, R1b_bar, R2aa_bar, R2bb_bar, R2ab_bar};
+    double* Tb[5] = {T1a_bar, T1b_bar, T2aa_bar, T2bb_bar, T2ab_bar};
+    if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) ||
+        (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
+        c->err = "invalid ref/method/mem_kind";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    int nrb = 0;
+    for (int k = 0; k < 5; ++k) {
+        if (!T[k] || !Tb[k]) {
+            c->err = "NULL amplitude or amplitude-gradient pointer";
+            return DCSD_ERR_INVALID_ARG;
+        }
+        nrb += Rb[k] != nullptr;
+    }
+    if (nrb != 0 && nrb != 5) {
+        c->err = "residual cotangents must be all NULL or all given";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    const size_t nn = (size_t)c->n * c->n, nB = (size_t)c->X * nn;
+    if (mem_kind == DCSD_MEM_DEVICE)
+        return vjp_run(c, ref, method, T, nrb ? Rb : nullptr, dEA_bar, W_bar, Tb, B_bar, fock_a_bar, fock_b_bar);
+    // host memory: stage through device buffers
+    DCSD_TRY(ensure_abi(c));
+    std::vector<double*> tmp;
+    struct Free {
+        std::vector<double*>& v;
+        ~Free() { for (double* p : v) cudaFree(p); }
+    } fr{tmp};
+    auto dev = [&](size_t n) -> double* {
+        double* p = nullptr;
+        if (alloc(c, &p, n) != DCSD_OK) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    const double* Td[5];
+    const double* Rd[5] = {};
+    double* Tbd[5];
+    for (int k = 0; k < 5; ++k) {
+        const size_t len = abi_len(c, k);
+        DCSD_CUDA(c, cudaMemcpyAsync(c->abi[k], T[k], len * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        Td[k] = c->abi[k];
+        if (nrb) {
+            DCSD_CUDA(c, cudaMemcpyAsync(c->abi[5 + k], Rb[k], len * sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream));
+            Rd[k] = c->abi[5 + k];
+        }
+        if (!(Tbd[k] = dev(len))) return DCSD_ERR_OOM;
+    }
+    double* Bd = nullptr;
+    double* Fad = nullptr;
+    double* Fbd = nullptr;
+    if (B_bar && !(Bd = dev(nB))) return DCSD_ERR_OOM;
+    if (fock_a_bar && !(Fad = dev(nn))) return DCSD_ERR_OOM;
+    if (fock_b_bar && !(Fbd = dev(nn))) return DCSD_ERR_OOM;
+    DCSD_TRY(vjp_run(c, ref, method, Td, nrb ? Rd : nullptr, dEA_bar, W_bar, Tbd, Bd, Fad, Fbd));
+    for (int k = 0; k < 5; ++k)
+        DCSD_CUDA(c, cudaMemcpyAsync(Tb[k], Tbd[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    if (Bd) DCSD_CUDA(c, cudaMemcpyAsync(B_bar, Bd, nB * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (Fad) DCSD_CUDA(c, cudaMemcpyAsync(fock_a_bar, Fad, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (Fbd) DCSD_CUDA(c, cudaMemcpyAsync(fock_b_bar, Fbd, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
     return DCSD_OK;
 }
 
@@ -529,6 +600,249 @@ static bool solve_small(int m, std::vector<double> A, std::vector<double> b, std
     }
     return true;
 }
+
+namespace {
+
+// same-spin blocks (0, 1) of a union [3][O][O][V][V] array projected onto
+// arrays antisymmetric in (i,j) and in (a,b)
+__global__ void k_antisym_ss(long O, long V, double* x) {
+    const long total = 2 * O * O * V * V;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long blk = e / (O * O * V * V), r = e - blk * O * O * V * V;
+        const long i = r / (O * V * V), j = (r / (V * V)) % O, a = (r / V) % V, b = r % V;
+        if (i > j || a > b) continue;  // one thread per quadruple
+        double* X = x + blk * O * O * V * V;
+        auto at = [&](long p, long q, long c, long d) -> double& { return X[((p * O + q) * V + c) * V + d]; };
+        if (i == j || a == b) {
+            at(i, j, a, b) = at(j, i, a, b) = at(i, j, b, a) = at(j, i, b, a) = 0.0;
+            continue;
+        }
+        const double v = 0.25 * (at(i, j, a, b) - at(j, i, a, b) - at(i, j, b, a) + at(j, i, b, a));
+        at(i, j, a, b) = v;
+        at(j, i, a, b) = -v;
+        at(i, j, b, a) = -v;
+        at(j, i, b, a) = v;
+    }
+}
+
+}  // namespace
+
+// Lambda equations of the Lagrangian L = E(T) + sum_q Lambda_q R_q(T) with
+// E = dE_A + state * W (state +1 singlet, -1 triplet), at converged T:
+//     dL/dT = dE/dT + Lambda^T dR/dT = 0,
+// solved by Jacobi steps with the amplitude denominators and DIIS; every
+// iteration is one reverse sweep of the recorded FP64 residual with seeds
+// (Lambda, 1, state).  The response density gamma^sigma_pq = dL/df^sigma_pq
+// is the Fock-matrix gradient of the final sweep.
+extern "C" dcsd_status dcsd_lambda(dcsd_ctx* h, const dcsd_solve_opts* o, int state, int mem_kind,
+                                   const double* T1a, const double* T1b, const double* T2aa, const double* T2bb,
+                                   const double* T2ab, double* L1a, double* L1b, double* L2aa, double* L2bb,
+                                   double* L2ab, double* rdm_a, double* rdm_b, dcsd_result* res) {
+    if (!h || !o || !res) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
+    double* Lio[5] = {L1a, L1b, L2aa, L2bb, L2ab};
+    if ((o->ref != 0 && o->ref != 1) || (o->method != DCSD_CCSD && o->method != DCSD_DCSD) ||
+        o->precision != DCSD_PREC_FP64 || o->maxiter < 1 || o->diis_n < 0 || o->diis_n > 16 || !(o->tol > 0.0) ||
+        (state != 1 && state != -1) || (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
+        c->err = "invalid Lambda options (precision must be FP64, state +1 or -1)";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 5; ++k)
+        if (!T[k] || !Lio[k]) {
+            c->err = "NULL amplitude or Lambda pointer";
+            return DCSD_ERR_INVALID_ARG;
+        }
+    auto t0 = std::chrono::steady_clock::now();
+    const int ref = o->ref;
+    const long n1 = 2l * c->O * c->V, len = n1 + 3l * c->O * c->O * c->V * c->V;
+    const size_t nn = (size_t)c->n * c->n;
+    std::vector<double*> tmp;
+    struct Free {
+        std::vector<double*>& v;
+        ~Free() { for (double* p : v) cudaFree(p); }
+    } fr{tmp};
+    auto dev = [&](size_t n) -> double* {
+        double* p = nullptr;
+        if (alloc(c, &p, n) != DCSD_OK) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    // amplitudes and Lambda guess on the device (ABI layout)
+    const double* Td[5];
+    double* Ld[5];
+    for (int k = 0; k < 5; ++k) {
+        const size_t l = abi_len(c, k);
+        if (mem_kind == DCSD_MEM_HOST) {
+            double* p = dev(l);
+            double* q = dev(l);
+            if (!p || !q) return DCSD_ERR_OOM;
+            DCSD_CUDA(c, cudaMemcpyAsync(p, T[k], l * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            if (o->use_guess)
+                DCSD_CUDA(c, cudaMemcpyAsync(q, Lio[k], l * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            Td[k] = p;
+            Ld[k] = q;
+        } else {
+            Td[k] = T[k];
+            Ld[k] = Lio[k];
+        }
+    }
+    double* lam = dev(len);   // union Lambda [t1-like | t2-like]
+    double* gp = dev(len);    // projected gradient
+    double* abt[5];           // ABI staging for the projection
+    for (int k = 0; k < 5; ++k)
+        if (!(abt[k] = dev(abi_len(c, k)))) return DCSD_ERR_OOM;
+    if (!lam || !gp) return DCSD_ERR_OOM;
+    DCSD_CUDA(c, cudaMemsetAsync(lam, 0, len * sizeof(double), c->stream));
+    if (o->use_guess) DCSD_TRY(layout_union(c, ref, 0, lam, lam + n1, Ld));
+    // record the residual at T
+    DCSD_TRY(unpack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]));
+    DCSD_TRY(vjp_record(c, ref, o->method));
+    struct TapeClear {
+        Ctx* c;
+        ~TapeClear() { c->tape.clear(); }
+    } tc_guard{c};
+    DCSD_TRY(sync_scalars(c, 2));
+    res->W = c->hostbuf[0];
+    res->dEA = c->hostbuf[1];
+    res->E_S = res->dEA + res->W;
+    res->E_T = res->dEA - res->W;
+    res->switched_at = -1;
+    res->polished_at = -1;
+    res->converged = 0;
+    const Frame frm = frame_of(c, ref);
+    const long eAB = n1 + (((2l * c->O + frm.occ_act[0]) * c->O + frm.occ_act[1]) * c->V + frm.vir_act[0]) * c->V +
+                     frm.vir_act[1];
+    const int nd = o->diis_n;
+    if (nd > 0 && c->diis_cap < nd) {
+        if (c->diis_t) cudaFree(c->diis_t);
+        if (c->diis_e) cudaFree(c->diis_e);
+        c->diis_t = c->diis_e = nullptr;
+        c->diis_cap = 0;
+        DCSD_TRY(alloc(c, &c->diis_t, (size_t)nd * len));
+        DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
+        c->diis_cap = nd;
+    }
+    double* sbuf = nd == 0 ? dev(len) : nullptr;
+    double* tbuf = nd == 0 ? dev(len) : nullptr;
+    if (nd == 0 && (!sbuf || !tbuf)) return DCSD_ERR_OOM;
+    const double* fa = c->fock[ref == 0 ? 0 : 1];
+    const double* fb = c->fock[ref == 0 ? 1 : 0];
+    std::vector<double> Bm(16 * 16, 0.0);
+    int nhist = 0, next = 0, it = 0;
+    dcsd_status status = DCSD_ERR_NOT_CONVERGED;
+    for (it = 1; it <= o->maxiter; ++it) {
+        DCSD_CUDA(c, cudaMemsetAsync(lam + eAB, 0, sizeof(double), c->stream));
+        DCSD_TRY(vjp_sweep(c, lam, lam + n1, 1.0, (double)state));
+        // gradient in the independent parameters: valid positions only, the
+        // same-spin doubles antisymmetric, the A->B double fixed
+        DCSD_TRY(layout_union(c, ref, 1, vjp_t1bar(c), vjp_t2bar(c), abt));
+        DCSD_CUDA(c, cudaMemsetAsync(gp, 0, len * sizeof(double), c->stream));
+        DCSD_TRY(layout_union(c, ref, 0, gp, gp + n1, abt));
+        k_antisym_ss<<<grid_n(c, 2l * c->O * c->O * c->V * c->V), 256, 0, c->stream>>>(c->O, c->V, gp + n1);
+        DCSD_TRY(launch_check(c, "antisym_ss"));
+        DCSD_CUDA(c, cudaMemsetAsync(gp + eAB, 0, sizeof(double), c->stream));
+        DCSD_TRY(maxabs(c, gp, len, c->scal + 21));
+        DCSD_TRY(sync_scalars(c, 22));
+        const double gmax = c->hostbuf[21];
+        res->max_r = gmax;
+        if (c->verbose) fprintf(stderr, "[dcsd lambda] it %3d max|G| %.3e\n", it, gmax);
+        if (!std::isfinite(gmax)) {
+            c->err = "non-finite Lambda gradient";
+            status = DCSD_ERR_NUMERIC;
+            break;
+        }
+        if (gmax <= o->tol) {
+            status = DCSD_OK;
+            res->converged = 1;
+            break;
+        }
+        double* st_v = nd > 0 ? c->diis_e + (size_t)next * len : sbuf;
+        double* tn_v = nd > 0 ? c->diis_t + (size_t)next * len : tbuf;
+        {
+            const size_t jsm = 2ul * c->V * sizeof(double);
+            const bool stage = jsm <= 48 * 1024;
+            const unsigned jg = (unsigned)std::min<long>(2l * c->O + 3l * c->O * c->O, (long)c->num_sms * 8);
+            k_jacobi_rows<false><<<jg, 256, stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb, lam,
+                                                                           gp, tn_v, st_v, stage);
+            DCSD_TRY(launch_check(c, "lambda_jacobi"));
+        }
+        if (nd == 0) {
+            DCSD_CUDA(c, cudaMemcpyAsync(lam, tn_v, len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            continue;
+        }
+        const int cur = next;
+        next = (next + 1) % nd;
+        nhist = std::min(nhist + 1, nd);
+        {
+            const double* ys[16];
+            for (int j = 0; j < nhist; ++j) ys[j] = c->diis_e + (size_t)((cur - j + nd) % nd) * len;
+            DCSD_TRY(multidot(c, st_v, ys, nhist, len, c->scal + 24));
+        }
+        DCSD_CUDA(c, cudaMemcpyAsync(c->hostbuf + 24, c->scal + 24, sizeof(double) * nhist, cudaMemcpyDeviceToHost,
+                                     c->stream));
+        DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int j = 0; j < nhist; ++j) {
+            const int sl = (cur - j + nd) % nd;
+            Bm[cur * 16 + sl] = Bm[sl * 16 + cur] = c->hostbuf[24 + j];
+        }
+        LinComb lc;
+        lc.m = 0;
+        if (nhist >= 2) {
+            const int m = nhist + 1;
+            std::vector<double> A(m * m, 0.0), bb(m, 0.0), xx;
+            std::vector<int> sl(nhist);
+            for (int j = 0; j < nhist; ++j) sl[j] = (cur - j + nd) % nd;
+            double scale = 0.0;
+            for (int a = 0; a < nhist; ++a) scale = std::max(scale, std::fabs(Bm[sl[a] * 16 + sl[a]]));
+            if (scale <= 0.0) scale = 1.0;
+            for (int a = 0; a < nhist; ++a)
+                for (int b = 0; b < nhist; ++b) A[a * m + b] = Bm[sl[a] * 16 + sl[b]] / scale;
+            for (int a = 0; a < nhist; ++a) { A[a * m + nhist] = -1.0; A[nhist * m + a] = -1.0; }
+            bb[nhist] = -1.0;
+            if (solve_small(m, A, bb, xx))
+                for (int j = 0; j < nhist; ++j) {
+                    lc.v[lc.m] = c->diis_t + (size_t)sl[j] * len;
+                    lc.coef[lc.m] = xx[j];
+                    lc.m++;
+                }
+        }
+        if (lc.m == 0) {
+            lc.v[0] = tn_v;
+            lc.coef[0] = 1.0;
+            lc.m = 1;
+        }
+        k_lincomb<<<grid_n(c, len), 256, 0, c->stream>>>(lc, len, lam);
+        DCSD_TRY(launch_check(c, "lambda_diis"));
+    }
+    res->iters = std::min(it, o->maxiter);
+    // outputs: Lambda (ABI) and the response density of the last sweep
+    DCSD_TRY(layout_union(c, ref, 1, lam, lam + n1, Ld));
+    if (mem_kind == DCSD_MEM_HOST)
+        for (int k = 0; k < 5; ++k)
+            DCSD_CUDA(c, cudaMemcpyAsync(Lio[k], Ld[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+    double* rd[2] = {rdm_a, rdm_b};
+    for (int s2 = 0; s2 < 2; ++s2)
+        if (rd[s2])
+            DCSD_CUDA(c, cudaMemcpyAsync(rd[s2], vjp_fbar(c, s2), nn * sizeof(double),
+                                         mem_kind == DCSD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                         c->stream));
+    DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+extern "C" dcsd_status dcsd_heff(double dEA, double W, double* H, double* evals, int* singlet_index) {
+    if (!H || !evals || !singlet_index) return DCSD_ERR_INVALID_ARG;
+    H[0] = dEA; H[1] = W; H[2] = W; H[3] = dEA;
+    double lo = dEA - std::fabs(W), hi = dEA + std::fabs(W);
+    evals[0] = lo;
+    evals[1] = hi;
+    *singlet_index = W >= 0.0 ? 1 : 0;  // the singlet is dEA + W
+    return DCSD_OK;
+}
+
 
 extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem_kind, double* T1a,
                                   double* T1b, double* T2aa, double* T2bb, double* T2ab, dcsd_result* res) {
@@ -578,8 +892,10 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     }
     std::vector<double> Bm(16 * 16, 0.0);
     int nhist = 0, next = 0;
+    // MIXED phases: 0 BF16, 1 BF16X6, 2 FP64
+    int phase = 0;
     bool switched = false;
-    int switched_at = -1;
+    int switched_at = -1, polished_at = -1;
     double best_r = 1e300, best_r_window = 1e300;
     int stall = 0;
     const double* fa = c->fock[ref == 0 ? 0 : 1];
@@ -592,10 +908,12 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     dcsd_status status = DCSD_ERR_NOT_CONVERGED;
     res->converged = 0;
     res->switched_at = -1;
+    res->polished_at = -1;
     int it = 0;
     for (it = 1; it <= o->maxiter; ++it) {
         int prec = o->precision;
-        if (prec == DCSD_PREC_MIXED) prec = switched ? DCSD_PREC_BF16X6 : DCSD_PREC_BF16;
+        if (prec == DCSD_PREC_MIXED)
+            prec = phase == 0 ? DCSD_PREC_BF16 : phase == 1 ? DCSD_PREC_BF16X6 : DCSD_PREC_FP64;
         dcsd_status s = residual_union(c, ref, o->method, prec);
         if (s != DCSD_OK) { status = s; break; }
         if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
@@ -621,13 +939,23 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         }
         // MIXED: leave BF16 once max|R| is below switch_tol or has stopped
         // decreasing (BF16 rounding puts a floor under the residual)
-        if (o->precision == DCSD_PREC_MIXED && !switched) {
+        if (o->precision == DCSD_PREC_MIXED && phase < 2) {
             best_r = std::min(best_r, rmax);
             if (rmax < best_r_window * 0.5) { best_r_window = rmax; stall = 0; }
             else ++stall;
-            if (rmax < o->switch_tol || stall >= 6) {
+            bool next_phase = false;
+            if (phase == 0 && (rmax < o->switch_tol || stall >= 6)) {
                 switched = true;
                 switched_at = it;
+                next_phase = true;
+            } else if (phase == 1 && o->polish_tol > 0.0 && (rmax < o->polish_tol || stall >= 4)) {
+                polished_at = it;
+                next_phase = true;
+            }
+            if (next_phase) {
+                ++phase;
+                stall = 0;
+                best_r_window = rmax;
                 nhist = 0;  // history built with the lower precision is discarded
                 next = 0;
             }
@@ -707,6 +1035,7 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     res->E_S = res->dEA + res->W;
     res->E_T = res->dEA - res->W;
     res->switched_at = switched_at;
+    res->polished_at = polished_at;
     // amplitudes out
     dcsd_status ps = pack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]);
     if (ps != DCSD_OK) return ps;

@@ -58,6 +58,51 @@ struct TcEngine;  // tensor-core contraction engine (tc_gemm.cu)
 // reduction scratch (Ctx::red), in doubles
 constexpr int kRedDoubles = 32768;
 
+// ---------------------------------------------------------------------------
+// reverse mode (vjp.cu): while Ctx::rec is set, the FP64 residual records
+// every operation on a tape and takes fresh buffers for its intermediates
+// from an arena, so that the reverse sweep sees each value as it was used.
+// ---------------------------------------------------------------------------
+enum TapeOpType {
+    OP_EINSUM,   // C = beta C + alpha einsum(spec)(A, B)
+    OP_AXPY,     // C = beta C + alpha A (strided views)
+    OP_AXPY4,    // C += sum_k al[k] X[k]
+    OP_COPY,     // C = A (same shape)
+    OP_ZERO,     // C = 0
+    OP_DOT,      // *p[0] = sum A B + beta * *p[0]
+    OP_TAU,      // iarg[0] = spin: A = S = 1 - tau, B = T = 1 + tau from t1
+    OP_FOCKHH,   // C = Wo -= delta F2 + delta F1 (A = F1, B = F2)
+    OP_ECOMB,    // dE_A from the energy pieces in scal[1..9]
+    OP_SWAPVIR,  // t2s = t2 with the virtual pair exchanged
+    OP_MTERMS,   // two-determinant coupling terms, iarg[0] = ref
+    OP_LADDER    // R2 += sum_cd t2 (ac|bd), integrals rebuilt in the reverse sweep
+};
+
+struct TapeOp {
+    int type = 0;
+    std::string spec;
+    double alpha = 0.0, beta = 0.0;
+    TV A, B, C;
+    int nv = 0;
+    TV X[4];
+    double al[4] = {};
+    int iarg[4] = {};
+    double* p[4] = {};
+};
+
+struct ArenaBlock {
+    double* fwd = nullptr;
+    double* adj = nullptr;
+    size_t cap = 0, used = 0;
+};
+
+// forward buffer and its adjoint (same element offsets)
+struct AdjRegion {
+    const double* fwd = nullptr;
+    size_t len = 0;
+    double* adj = nullptr;
+};
+
 struct Ctx {
     int nc = 0, nv = 0, X = 0;
     int n = 0, O = 0, V = 0;      // n = nc+2+nv; union occ O = nc+2; union vir V = nv+2
@@ -126,6 +171,14 @@ struct Ctx {
     bool verbose = false;         // DCSD_VERBOSE=1: per-iteration solver log on stderr
     std::string cur_spec;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
+
+    // reverse mode
+    bool rec = false;
+    std::vector<TapeOp> tape;
+    std::vector<ArenaBlock> arena;
+    std::vector<AdjRegion> regions;
+    double* vbuf = nullptr;       // adjoint buffers of the inputs and outputs (vjp.cu)
+    size_t vbuf_elems = 0;
 
     // solver state (device)
     double* diis_t = nullptr;     // [nd][len]
@@ -223,6 +276,34 @@ dcsd_status apply_mterms(Ctx* c, int ref, bool fp32);
 
 // residual orchestration (residual.cu)
 dcsd_status residual_union(Ctx* c, int ref, int method, int precision);
+// reverse mode helpers (vjp.cu)
+// buffer for an intermediate: `normal` outside recording, a fresh arena block
+// (with a zeroed adjoint twin) while recording
+double* scratch(Ctx* c, double* normal, size_t elems);
+void rec_push(Ctx* c, TapeOp&& op);
+// device copy / zero fill that the tape records
+dcsd_status copy_dev(Ctx* c, double* dst, const double* src, size_t n);
+dcsd_status zero_dev(Ctx* c, double* dst, size_t n);
+inline bool recording(const Ctx* c) { return c->rec; }
+// FP64 ladder R2 += sum_cd t2 (ac|bd) (chunked, integrals never stored)
+dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk);
+void vjp_free(Ctx* c);
+// reverse mode in stages: record the FP64 residual at c->t1/c->t2, then any
+// number of reverse sweeps with union-layout seeds; the gradients of the
+// last sweep are at vjp_t1bar/vjp_t2bar (union layout) and vjp_fbar
+dcsd_status vjp_record(Ctx* c, int ref, int method);
+dcsd_status vjp_sweep(Ctx* c, const double* R1bar_u, const double* R2bar_u, double Ebar, double Wbar);
+double* vjp_t1bar(Ctx* c);
+double* vjp_t2bar(Ctx* c);
+double* vjp_fbar(Ctx* c, int spin);
+// adjoints of the coupling terms and of t2s (mterm.cu); pointers are the
+// adjoint buffers of t1, t2, t2s, c1, R1, R2 and the scalars
+dcsd_status mterms_adjoint(Ctx* c, int ref, double* t1b, double* t2b, double* t2sb, double* c1b, double* R1b,
+                           double* R2b, double* scalb);
+dcsd_status swap_vir_adjoint(Ctx* c, const double* t2sb, double* t2b);
+// ABI <-> union amplitude layout for explicit union buffers (dir 0: ABI ->
+// union, the caller zeroes the union buffers first; dir 1: union -> ABI)
+dcsd_status layout_union(Ctx* c, int ref, int dir, double* u1, double* u2, double* const* abi);
 dcsd_status add_fock_hh(Ctx* c, double* Wo, const double* F1, const double* F2);
 dcsd_status init_constants(Ctx* c);
 

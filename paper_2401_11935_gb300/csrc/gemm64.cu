@@ -440,6 +440,17 @@ dcsd_status einsum32(Ctx* c, const char* spec, double alpha, const TV& A, const 
 
 static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
                                double beta, const TV& C, bool fp32) {
+    if (c->rec && !fp32) {
+        TapeOp op;
+        op.type = OP_EINSUM;
+        op.spec = spec;
+        op.alpha = alpha;
+        op.beta = beta;
+        op.A = A;
+        op.B = B;
+        op.C = C;
+        rec_push(c, std::move(op));
+    }
     GemmArgs g;
     std::string err;
     if (!plan_einsum(spec, A, B, C, g.p, err)) {
@@ -591,6 +602,15 @@ static unsigned grid_for(Ctx* c, long total) {
 }
 
 dcsd_status axpy_view(Ctx* c, double alpha, const TV& A, double beta, const TV& C) {
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_AXPY;
+        op.alpha = alpha;
+        op.beta = beta;
+        op.A = A;
+        op.C = C;
+        rec_push(c, std::move(op));
+    }
     EwArgs a;
     if (!ew_setup(c, A, C, a)) return DCSD_ERR_INVALID_ARG;
     if (a.total == 0) return DCSD_OK;
@@ -634,6 +654,17 @@ __global__ void __launch_bounds__(256) k_axpy4(Axpy4Args a) {
 }
 
 dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C) {
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_AXPY4;
+        op.nv = std::min(nv, 4);
+        for (int k = 0; k < op.nv; ++k) {
+            op.X[k] = A[k];
+            op.al[k] = alpha[k];
+        }
+        op.C = C;
+        rec_push(c, std::move(op));
+    }
     Axpy4Args a;
     if (C.rank != 4 || nv < 1 || nv > 4) {
         c->err = "axpy4 needs rank-4 views";
@@ -779,6 +810,15 @@ __global__ void k_dot_final(const double* partial, int n, double* out, double ac
 }
 
 dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accumulate) {
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_DOT;
+        op.A = A;
+        op.B = B;
+        op.beta = accumulate;
+        op.p[0] = out;
+        rec_push(c, std::move(op));
+    }
     EwArgs a;
     if (!ew_setup(c, A, B, a)) return DCSD_ERR_INVALID_ARG;
     a.A = A.p;
@@ -877,6 +917,13 @@ dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b, cons
     return launch_check(c, "unpack_T");
 }
 
+dcsd_status layout_union(Ctx* c, int ref, int dir, double* u1, double* u2, double* const* abi) {
+    LayoutArgs L = layout_args(c, ref);
+    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
+    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, dir, u1, u2, abi[0], abi[1], abi[2], abi[3], abi[4]);
+    return launch_check(c, "layout_union");
+}
+
 dcsd_status pack_R(Ctx* c, int ref, double* R1a, double* R1b, double* R2aa, double* R2bb,
                    double* R2ab) {
     LayoutArgs L = layout_args(c, ref);
@@ -910,6 +957,14 @@ __global__ void k_tau_mats(int n, int nc, int O, int V, const double* t1s, doubl
 }
 
 dcsd_status build_tau_mats(Ctx* c, int spin, double* Smat, double* Tmat) {
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_TAU;
+        op.iarg[0] = spin;
+        op.A = view(Smat, {(long)c->n, (long)c->n});
+        op.B = view(Tmat, {(long)c->n, (long)c->n});
+        rec_push(c, std::move(op));
+    }
     k_tau_mats<<<grid_for(c, (long)c->n * c->n), 256, 0, c->stream>>>(
         c->n, c->nc, c->O, c->V, c->t1 + (long)spin * c->O * c->V, Smat, Tmat);
     return launch_check(c, "tau_mats");

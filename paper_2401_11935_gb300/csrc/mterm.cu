@@ -787,6 +787,178 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode of the coupling terms (FP64).  For an element e with
+// cotangent g of its residual, R -= W (c - tc) gives W_bar -= g (c - tc),
+// c_bar = -W g and tc_bar = W g; c_bar flows to every factor of every term
+// of c (product rule), tc_bar to t1 and c1.  Factors are shared between
+// elements, so their adjoints accumulate with atomics.
+// ---------------------------------------------------------------------------
+struct MAdjPtrs {
+    double* t1;   // [2][O][V]
+    double* t2;   // [3][O][O][V][V]
+    double* t2s;  // [3][O][O][V][V] (virtuals exchanged)
+    double* c1;   // [2][O][V]
+    double* R1;
+    double* R2;
+    double* scal;  // scal_bar[0] = W_bar
+};
+
+__device__ __forceinline__ void eval_class_adj(const MArgs& a, const MAdjPtrs& d, int cls, const int q[4],
+                                               double coef) {
+    const long O = a.O, V = a.V, nb = O * O * V * V;
+    const int pos[8] = {q[0], q[1], q[2], q[3], a.nc, a.nc + 1, 0, 1};
+    const int o = c_off[a.ref][cls], n = c_cnt[a.ref][cls];
+    for (int k = 0; k < n; ++k) {
+        const MTerm& m = c_terms[a.ref][o + k];
+        double val[4];
+        double* adr[4];
+        for (int f = 0; f < m.nf; ++f) {
+            const MFac& g = m.f[f];
+            const int x0 = pos[g.idx[0]], x1 = pos[g.idx[1]];
+            if (g.arr < 2) {
+                const long ix = ((long)g.arr * O + x0) * V + x1;
+                val[f] = a.t1[ix];
+                adr[f] = d.t1 + ix;
+            } else {
+                const int x2 = pos[g.idx[2]], x3 = pos[g.idx[3]];
+                const long ix = (((long)x0 * O + x1) * V + x2) * V + x3;
+                if (g.arr < 5) {
+                    val[f] = a.t2[(g.arr - 2) * nb + ix];
+                    adr[f] = d.t2 + (g.arr - 2) * nb + ix;
+                } else {
+                    val[f] = a.t2s[(g.arr - 5) * nb + ix];
+                    adr[f] = d.t2s + (g.arr - 5) * nb + ix;
+                }
+            }
+        }
+        for (int f = 0; f < m.nf; ++f) {
+            double prod = coef * (double)m.sign;
+            for (int h = 0; h < m.nf; ++h)
+                if (h != f) prod *= val[h];
+            if (prod != 0.0) atomicAdd(adr[f], prod);
+        }
+    }
+}
+
+__device__ __forceinline__ void block_add(double v, double* target) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(target, v);
+}
+
+__global__ void __launch_bounds__(256) k_mterm_doubles_adj(MArgs a, MAdjPtrs d) {
+    const long O = a.O, V = a.V, VV = V * V, total = 3 * O * O * VV;
+    const double W = *a.W;
+    const double* t1a = a.t1;
+    const double* t1b = a.t1 + O * V;
+    const double* c1a = a.c1;
+    const double* c1b = a.c1 + O * V;
+    double wbar = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long slot = e / VV, ab = e - slot * VV;
+        const int blk = (int)(slot / (O * O)), i = (int)((slot / O) % O), j = (int)(slot % O);
+        const int x = (int)(ab / V), b = (int)(ab % V);
+        const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+        bool ok = occ_ok(a, s1, i) && occ_ok(a, s2, j) && vir_ok(a, s1, x) && vir_ok(a, s2, b);
+        if (blk != 2 && (i == j || x == b)) ok = false;
+        const bool ai = i == a.occ_act[s1], aj = j == a.occ_act[s2];
+        const bool aa = x == a.vir_act[s1], abv = b == a.vir_act[s2];
+        if (blk == 2 && ai && aj && aa && abv) ok = false;  // the A->B element
+        if (!ok) {
+            d.R2[e] = 0.0;  // the forward overwrote these elements
+            continue;
+        }
+        const double g = d.R2[e];
+        if (g == 0.0) continue;
+        const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + abv;
+        const int q[4] = {i, j, x, b};
+        const double c2 = eval_class(a, cls, q);
+        double tc;
+        const double* tA = blk == 1 ? t1b : t1a;
+        const double* cA = blk == 1 ? c1b : c1a;
+        const double* tB = blk == 0 ? t1a : t1b;
+        const double* cB = blk == 0 ? c1a : c1b;
+        const long sA = blk == 1 ? O * V : 0, sB = blk == 0 ? 0 : O * V;
+        const double tb = W * g;  // tc_bar
+        if (blk == 2) {
+            tc = t1a[i * V + x] * c1b[j * V + b] + t1b[j * V + b] * c1a[i * V + x];
+            atomicAdd(d.t1 + i * V + x, tb * c1b[j * V + b]);
+            atomicAdd(d.c1 + O * V + j * V + b, tb * t1a[i * V + x]);
+            atomicAdd(d.t1 + O * V + j * V + b, tb * c1a[i * V + x]);
+            atomicAdd(d.c1 + i * V + x, tb * t1b[j * V + b]);
+        } else {
+            tc = tA[i * V + x] * cB[j * V + b] - tA[j * V + x] * cB[i * V + b] - tB[i * V + b] * cA[j * V + x] +
+                 tB[j * V + b] * cA[i * V + x];
+            atomicAdd(d.t1 + sA + i * V + x, tb * cB[j * V + b]);
+            atomicAdd(d.c1 + sB + j * V + b, tb * tA[i * V + x]);
+            atomicAdd(d.t1 + sA + j * V + x, -tb * cB[i * V + b]);
+            atomicAdd(d.c1 + sB + i * V + b, -tb * tA[j * V + x]);
+            atomicAdd(d.t1 + sB + i * V + b, -tb * cA[j * V + x]);
+            atomicAdd(d.c1 + sA + j * V + x, -tb * tB[i * V + b]);
+            atomicAdd(d.t1 + sB + j * V + b, tb * cA[i * V + x]);
+            atomicAdd(d.c1 + sA + i * V + x, tb * tB[j * V + b]);
+        }
+        wbar -= g * (c2 - tc);
+        eval_class_adj(a, d, cls, q, -W * g);
+    }
+    block_add(wbar, d.scal);
+}
+
+__global__ void __launch_bounds__(256) k_mterm_singles_adj(MArgs a, MAdjPtrs d) {
+    const long total = 2l * a.O * a.V;
+    const double W = *a.W;
+    double wbar = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / ((long)a.O * a.V));
+        const int i = (int)((e / a.V) % a.O), x = (int)(e % a.V);
+        if (!(occ_ok(a, s, i) && vir_ok(a, s, x))) {
+            d.R1[e] = 0.0;
+            continue;
+        }
+        const double g = d.R1[e];
+        wbar -= g * a.c1[e];
+        const double cbar = d.c1[e] - W * g;
+        if (cbar == 0.0) continue;
+        const int cls = 48 + s * 4 + ((i == a.occ_act[s]) << 1) + (x == a.vir_act[s]);
+        const int q[4] = {i, x, 0, 0};
+        eval_class_adj(a, d, cls, q, cbar);
+    }
+    block_add(wbar, d.scal);
+}
+
+// t2_bar[blk][i][j][a][b] += t2s_bar[blk][i][j][b][a]
+__global__ void k_swap_vir_adj(long nmat, int V, const double* t2sb, double* t2b) {
+    const long total = nmat * V * V;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long mat = e / ((long)V * V), r = e - mat * V * V;
+        const int x = (int)(r / V), b = (int)(r % V);
+        t2b[e] += t2sb[mat * V * V + (long)b * V + x];
+    }
+}
+
+dcsd_status mterms_adjoint(Ctx* c, int ref, double* t1b, double* t2b, double* t2sb, double* c1b, double* R1b,
+                           double* R2b, double* scalb) {
+    MArgs a;
+    a.O = c->O; a.V = c->V; a.nc = c->nc; a.ref = ref;
+    Frame f = frame_of(c, ref);
+    for (int s = 0; s < 2; ++s) { a.occ_act[s] = f.occ_act[s]; a.vir_act[s] = f.vir_act[s]; }
+    a.t1 = c->t1; a.t2 = c->t2; a.t2s = c->t2s; a.R1 = c->R1; a.R2 = c->R2; a.c1 = c->c1;
+    a.W = c->scal;
+    MAdjPtrs d{t1b, t2b, t2sb, c1b, R1b, R2b, scalb};
+    const unsigned g = (unsigned)std::max(1, c->num_sms * 8);
+    // doubles first: they add to c1_bar, which the singles then propagate
+    k_mterm_doubles_adj<<<g, 256, 0, c->stream>>>(a, d);
+    DCSD_TRY(launch_check(c, "mterm_doubles_adj"));
+    k_mterm_singles_adj<<<g, 256, 0, c->stream>>>(a, d);
+    return launch_check(c, "mterm_singles_adj");
+}
+
+dcsd_status swap_vir_adjoint(Ctx* c, const double* t2sb, double* t2b) {
+    k_swap_vir_adj<<<(unsigned)std::max(1, c->num_sms * 8), 256, 0, c->stream>>>(3l * c->O * c->O, c->V, t2sb,
+                                                                                t2b);
+    return launch_check(c, "swap_vir_adj");
+}
+
 // t2s[blk][i][j][b][a] = t2[blk][i][j][a][b] (32x32 tiles through shared memory)
 __global__ void k_swap_vir(long nmat, int V, const double* t2, double* t2s) {
     __shared__ double tile[32][33];
@@ -810,6 +982,15 @@ __global__ void k_swap_vir(long nmat, int V, const double* t2, double* t2s) {
 }
 
 dcsd_status apply_mterms(Ctx* c, int ref, bool fp32) {
+    if (c->rec) {
+        TapeOp sw;
+        sw.type = OP_SWAPVIR;
+        rec_push(c, std::move(sw));
+        TapeOp op;
+        op.type = OP_MTERMS;
+        op.iarg[0] = ref;
+        rec_push(c, std::move(op));
+    }
     MArgs a;
     a.O = c->O; a.V = c->V; a.nc = c->nc; a.ref = ref;
     Frame f = frame_of(c, ref);

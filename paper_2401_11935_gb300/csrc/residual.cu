@@ -67,6 +67,15 @@ __global__ void k_add_fock_hh(int O, double* Wo, const double* F1, const double*
 }
 
 dcsd_status add_fock_hh(Ctx* c, double* Wo, const double* F1, const double* F2) {
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_FOCKHH;
+        const long O = c->O;
+        op.C = view(Wo, {O, O, O, O});
+        op.A = view((double*)F1, {O, O});
+        op.B = view((double*)F2, {O, O});
+        rec_push(c, std::move(op));
+    }
     const long total = (long)c->O * c->O * c->O * c->O;
     k_add_fock_hh<<<(unsigned)std::max<long>(1, std::min<long>((total + 255) / 256, 4096)), 256, 0,
                     c->stream>>>(c->O, Wo, F1, F2);
@@ -133,24 +142,24 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     TV t2 = view(c->t2, {3, O, O, V, V});
     TV R1 = view(c->R1, {2, O, V});
     TV R2 = view(c->R2, {3, O, O, V, V});
-    TV Bd = view(c->Bd, {2, X, n, n});
-    TV Z = view(c->Z, {2, X, O, V});
+    const size_t nn2 = (size_t)n * n;
+    // intermediates (fresh buffers while recording for the reverse sweep)
+    TV Bd = view(scratch(c, c->Bd, 2 * X * nn2), {2, X, n, n});
+    TV Z = view(scratch(c, c->Z, 2 * X * O * V), {2, X, O, V});
     TV J = view(c->J, {O, O, V, V});
-    TV fd = view(c->fd, {2, n, n});
+    TV fd = view(scratch(c, c->fd, 2 * nn2), {2, n, n});
     auto BdVO = [&](int s) { return sub(sub(blk(Bd, s), 1, nc, V), 2, 0, O); };  // [L][a][i]
     auto BdOO = [&](int s) { return sub(sub(blk(Bd, s), 1, 0, O), 2, 0, O); };  // [L][k][i]
     auto BdVV = [&](int s) { return sub(sub(blk(Bd, s), 1, nc, V), 2, nc, V); };  // [L][a][c]
     const double* fock_s[2] = {c->fock[ref == 0 ? 0 : 1], c->fock[ref == 0 ? 1 : 0]};
-    const size_t nn2 = (size_t)n * n;
 
     // ---- T1 dressing of the DF factors -----------------------------------
     for (int s = 0; s < 2; ++s) {
         TV t1s = blk(t1, s);
-        TV P = view(c->Pbt, {X, n, O});
+        TV P = view(scratch(c, c->Pbt, X * n * O), {X, n, O});
         DCSD_TRY(sml("Lpa,ka->Lpk", 1.0, sub(B, 2, nc, V), t1s, 0.0, P));
         TV Bds = blk(Bd, s);
-        DCSD_CUDA(c, cudaMemcpyAsync(Bds.p, c->B, sizeof(double) * X * nn2, cudaMemcpyDeviceToDevice,
-                                     c->stream));
+        DCSD_TRY(copy_dev(c, Bds.p, c->B, X * nn2));
         DCSD_TRY(axpy_view(c, 1.0, P, 1.0, sub(Bds, 2, 0, O)));
         DCSD_TRY(sml("ka,Lkq->Laq", -1.0, t1s, sub(B, 1, 0, O), 1.0, sub(Bds, 1, nc, V)));
         DCSD_TRY(sml("ka,Lkm->Lam", -1.0, t1s, sub(P, 1, 0, O), 1.0, sub(sub(Bds, 1, nc, V), 2, 0, O)));
@@ -158,21 +167,21 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
 
     // ---- dressed Fock matrices -------------------------------------------
     {
-        TV jv = view(c->fsc + 7 * nn2, {X});
+        TV jv = view(scratch(c, c->fsc + 7 * nn2, X), {X});
         TV Bova = sub(sub(B, 1, 0, O), 2, nc, V);
         DCSD_TRY(sml("Lka,ka->L", 1.0, Bova, blk(t1, 0), 0.0, jv));
         DCSD_TRY(sml("Lka,ka->L", 1.0, Bova, blk(t1, 1), 1.0, jv));
-        TV Jt = view(c->fsc, {n, n});
+        TV Jt = view(scratch(c, c->fsc, nn2), {n, n});
         DCSD_TRY(sml("Lpq,L->pq", 1.0, B, jv, 0.0, Jt));
         for (int s = 0; s < 2; ++s) {
-            TV F1 = view(c->fsc + 1 * nn2, {n, n});
-            DCSD_CUDA(c, cudaMemcpyAsync(F1.p, fock_s[s], sizeof(double) * nn2, cudaMemcpyDeviceToDevice,
-                                         c->stream));
+            TV F1 = view(scratch(c, c->fsc + 1 * nn2, nn2), {n, n});
+            DCSD_TRY(copy_dev(c, F1.p, fock_s[s], nn2));
             DCSD_TRY(axpy_view(c, 1.0, view(c->Kref[ref][s], {n, n}), 1.0, F1));
             DCSD_TRY(axpy_view(c, 1.0, Jt, 1.0, F1));
-            TV S = view(c->fsc + 2 * nn2, {n, n}), Tm = view(c->fsc + 3 * nn2, {n, n});
+            TV S = view(scratch(c, c->fsc + 2 * nn2, nn2), {n, n});
+            TV Tm = view(scratch(c, c->fsc + 3 * nn2, nn2), {n, n});
             DCSD_TRY(build_tau_mats(c, s, S.p, Tm.p));
-            TV tmp = view(c->fsc + 4 * nn2, {n, n});
+            TV tmp = view(scratch(c, c->fsc + 4 * nn2, nn2), {n, n});
             DCSD_TRY(sml("pr,rq->pq", 1.0, F1, Tm, 0.0, tmp));
             TV fds = blk(fd, s);
             DCSD_TRY(sml("pr,rq->pq", 1.0, S, tmp, 0.0, fds));
@@ -190,7 +199,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     DCSD_TRY(big("ikac,Lkc->Lia", 1.0, blk(t2, 1), Bov, 0.0, blk(Z, 1)));
     DCSD_TRY(big("kica,Lkc->Lia", 1.0, blk(t2, 2), Bov, 1.0, blk(Z, 1)));
 
-    DCSD_CUDA(c, cudaMemsetAsync(c->R2, 0, sizeof(double) * 3 * O * O * V * V, c->stream));
+    DCSD_TRY(zero_dev(c, c->R2, 3 * O * O * V * V));
     // tensor-core modes: accumulate the tensor-core contributions to R2 in FP32
     struct R2fGuard {
         Ctx* c;
@@ -218,7 +227,8 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     }
 
     // ---- Fock terms incl. the Fock-like quadratic terms ---------------------
-    TV Foc = view(c->Foc, {2, O, O}), Fvi = view(c->Fvi, {2, V, V});
+    TV Foc = view(scratch(c, c->Foc, 2 * O * O), {2, O, O});
+    TV Fvi = view(scratch(c, c->Fvi, 2 * V * V), {2, V, V});
     for (int s = 0; s < 2; ++s) {
         TV fds = blk(fd, s);
         DCSD_TRY(sml("Lme,Lje->mj", y, Bov, blk(Z, s), 0.0, blk(Foc, s)));
@@ -233,25 +243,20 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     }
 
     // ---- particle-particle ladder (undressed (ac|bd), stacked blocks) --------
-    TV G = view(c->G, {4, O, O, O, V});
-    TV H = view(c->H, {3, O, O, O, O});
+    TV G = view(scratch(c, c->G, 4 * O * O * O * V), {4, O, O, O, V});
+    TV H = view(scratch(c, c->H, 3 * O * O * O * O), {3, O, O, O, O});
     if (prec != DCSD_PREC_FP64) {
-        DCSD_TRY(ladder_tc(c, nsplit, c->R2, c->G));
+        DCSD_TRY(ladder_tc(c, nsplit, c->R2, G.p));
     } else {
-        long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
-        for (long a0 = 0; a0 < V; a0 += ch) {
-            long na = std::min(ch, V - a0);
-            TV Vc = view(c->big0, {na, V, V, V});  // [a][c][b][d] = (ac|bd)
-            DCSD_TRY(big("Lac,Lbd->acbd", 1.0, sub(Bvv, 1, a0, na), Bvv, 0.0, Vc));
-            DCSD_TRY(big("sijcd,acbd->sijab", 1.0, t2, Vc, 1.0, sub(R2, 3, a0, na)));
-        }
+        const long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
+        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch));
     // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with t_ab
     // transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
     {
         long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
         for (long k0 = 0; k0 < O; k0 += kc) {
             long nk = std::min(kc, O - k0);
-            TV Ic = view(c->big0, {nk, V, V, V});  // [k][c][b][d]
+            TV Ic = view(scratch(c, c->big0, nk * V * V * V), {nk, V, V, V});  // [k][c][b][d]
             DCSD_TRY(big("Lkc,Lbd->kcbd", 1.0, sub(Bov, 1, k0, nk), Bvv, 0.0, Ic));
             DCSD_TRY(big("sijcd,kcbd->sijkb", 1.0, t2, Ic, 0.0, sub(sub(G, 0, 0, 3), 3, k0, nk)));
             DCSD_TRY(big("ijdc,kcbd->ijkb", 1.0, blk(t2, 2), Ic, 0.0, sub(blk(G, 3), 2, k0, nk)));
@@ -264,7 +269,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         DCSD_TRY(sml("ka,ijkb->ijab", -1.0, blk(t1, s1), blk(G, b), 1.0, blk(R2, b)));
         if (s1 == s2) DCSD_TRY(sml("mb,ijma->ijab", 1.0, blk(t1, s2), blk(G, b), 1.0, blk(R2, b)));
         else DCSD_TRY(sml("mb,ijma->ijab", -1.0, blk(t1, s2), blk(G, 3), 1.0, blk(R2, b)));
-        TV tmp = view(c->big1, {O, O, O, V});
+        TV tmp = view(scratch(c, c->big1, O * O * O * V), {O, O, O, V});
         DCSD_TRY(sml("ijkm,mb->ijkb", 1.0, blk(H, b), blk(t1, s2), 0.0, tmp));
         DCSD_TRY(sml("ka,ijkb->ijab", 1.0, blk(t1, s1), tmp, 1.0, blk(R2, b)));
     }
@@ -273,18 +278,19 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     for (int b = 0; b < 3; ++b) {
         int s1 = s1_of[b], s2 = s2_of[b];
         double cs = s1 == s2 ? 0.5 : 1.0;
-        TV Wo = view(c->Wo, {O, O, O, O});
+        TV Wo = view(scratch(c, c->Wo, O * O * O * O), {O, O, O, O});
         DCSD_TRY(sml("Lki,Llj->klij", 1.0, BdOO(s1), BdOO(s2), 0.0, Wo));
         DCSD_TRY(axpy_view(c, cs, perm(blk(H, b), {2, 3, 0, 1}), 1.0, Wo));
         // occupied Fock terms -P(ij) sum_k F_kj t_ik^ab as part of the same
         // contraction: Wo[k][l][i][j] -= d_ki F2[l][j] + d_lj F1[k][i]
-        DCSD_TRY(add_fock_hh(c, Wo.p, c->Foc + (long)s1 * O * O, c->Foc + (long)s2 * O * O));
+        DCSD_TRY(add_fock_hh(c, Wo.p, Foc.p + (long)s1 * O * O, Foc.p + (long)s2 * O * O));
         DCSD_TRY(big("klij,klab->ijab", 1.0, Wo, blk(t2, b), 1.0, blk(R2, b)));
     }
 
     // ---- ring (particle-hole) terms ------------------------------------------
     {
-        TV Uex[2] = {view(c->big0, {O, V, O, V}), view(c->big1, {O, V, O, V})};  // (kj|bc) as [k][c][j][b]
+        TV Uex[2] = {view(scratch(c, c->big0, O * V * O * V), {O, V, O, V}),
+                     view(scratch(c, c->big1, O * V * O * V), {O, V, O, V})};  // (kj|bc) as [k][c][j][b]
         for (int s = 0; s < 2; ++s) DCSD_TRY(big("Lkj,Lbc->kcjb", 1.0, BdOO(s), BdVV(s), 0.0, Uex[s]));
         TV Kq = perm(J, {0, 1, 3, 2});  // [k][l][c][d] = (kd|lc)
         auto Tm = [&](int sg, int tg) -> TV {
@@ -292,17 +298,17 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
             if (sg == 0) return blk(t2, 2);
             return perm(blk(t2, 2), {1, 0, 3, 2});
         };
-        TV Xacc = view(c->big2, {O, V, O, V});
-        TV scr = view(c->big3, {O, V, O, V});
         for (int sg = 0; sg < 2; ++sg)
             for (int sp = 0; sp < 2; ++sp) {
-                TV Ycol = view(c->big3, {X, O, V});
+                TV Xacc = view(scratch(c, c->big2, O * V * O * V), {O, V, O, V});
+                TV Ycol = view(scratch(c, c->big3, X * O * V), {X, O, V});
                 DCSD_TRY(axpy_view(c, 1.0, perm(BdVO(sp), {0, 2, 1}), 0.0, Ycol));
                 DCSD_TRY(axpy_view(c, 0.5, blk(Z, sp), 1.0, Ycol));
                 DCSD_TRY(big("Lia,Ljb->iajb", 1.0, blk(Z, sg), Ycol, 0.0, Xacc));
                 for (int tg = 0; tg < 2; ++tg) {
                     if (tg == sp) DCSD_TRY(big("ikac,kcjb->iajb", -1.0, Tm(sg, tg), Uex[tg], 1.0, Xacc));
                     if (x != 0.0) {
+                        TV scr = view(scratch(c, c->big3, O * V * O * V), {O, V, O, V});
                         DCSD_TRY(big("klcd,jlbd->kcjb", 1.0, Kq, Tm(sp, tg), 0.0, scr));
                         DCSD_TRY(big("ikac,kcjb->iajb", -0.5 * x, Tm(sg, tg), scr, 1.0, Xacc));
                     }
@@ -320,11 +326,11 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
                 }
             }
         // mixed-spin pairs of the alpha-beta block
-        TV M1 = view(c->big0, {O, V, O, V});  // [k][c][i][b]
+        TV M1 = view(scratch(c, c->big0, O * V * O * V), {O, V, O, V});  // [k][c][i][b]
         DCSD_TRY(big("Lki,Lbc->kcib", -1.0, BdOO(0), BdVV(1), 0.0, M1));
         if (x != 0.0) DCSD_TRY(big("kldc,ildb->kcib", 0.5 * x, J, blk(t2, 2), 1.0, M1));
         DCSD_TRY(big("kjac,kcib->ijab", 1.0, blk(t2, 2), M1, 1.0, blk(R2, 2)));
-        TV M2 = view(c->big1, {O, V, O, V});  // [k][c][j][a]
+        TV M2 = view(scratch(c, c->big1, O * V * O * V), {O, V, O, V});  // [k][c][j][a]
         DCSD_TRY(big("Lkj,Lac->kcja", -1.0, BdOO(1), BdVV(0), 0.0, M2));
         if (x != 0.0) DCSD_TRY(big("kldc,ljad->kcja", 0.5 * x, J, blk(t2, 2), 1.0, M2));
         DCSD_TRY(big("ikcb,kcja->ijab", 1.0, blk(t2, 2), M2, 1.0, blk(R2, 2)));
@@ -353,15 +359,23 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
             DCSD_TRY(dot_view(c, fo, blk(t1, sp), s + 1, sp == 0 ? 0.0 : 1.0));
         }
         for (int b = 0; b < 3; ++b) DCSD_TRY(dot_view(c, J, blk(t2, b), s + 2 + b, 0.0));
-        TV u = view(c->fsc + 5 * nn2, {O, V});
+        auto ubuf = [&]() { return view(scratch(c, c->fsc + 5 * nn2, O * V), {O, V}); };
         for (int sp = 0; sp < 2; ++sp) {
+            TV u = ubuf();
             DCSD_TRY(einsum64(c, "ijab,jb->ia", 1.0, J, blk(t1, sp), 0.0, u));
             DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 5 + 2 * sp, 0.0));
-            DCSD_TRY(einsum64(c, "ijab,ja->ib", 1.0, J, blk(t1, sp), 0.0, u));
-            DCSD_TRY(dot_view(c, u, blk(t1, sp), s + 6 + 2 * sp, 0.0));
+            TV u2 = ubuf();
+            DCSD_TRY(einsum64(c, "ijab,ja->ib", 1.0, J, blk(t1, sp), 0.0, u2));
+            DCSD_TRY(dot_view(c, u2, blk(t1, sp), s + 6 + 2 * sp, 0.0));
         }
+        TV u = ubuf();
         DCSD_TRY(einsum64(c, "ijab,jb->ia", 1.0, J, blk(t1, 1), 0.0, u));
         DCSD_TRY(dot_view(c, u, blk(t1, 0), s + 9, 0.0));
+        if (c->rec) {
+            TapeOp op;
+            op.type = OP_ECOMB;
+            rec_push(c, std::move(op));
+        }
         k_energy_combine<<<1, 1, 0, c->stream>>>(s);
         DCSD_TRY(launch_check(c, "energy_combine"));
     }
@@ -374,8 +388,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     // ---- W = R^X at the A->B double; two-determinant terms ------------------------
     {
         long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
-        DCSD_CUDA(c, cudaMemcpyAsync(c->scal, c->R2 + e, sizeof(double), cudaMemcpyDeviceToDevice,
-                                     c->stream));
+        DCSD_TRY(copy_dev(c, c->scal, c->R2 + e, 1));
     }
     DCSD_TRY(apply_mterms(c, ref, prec != DCSD_PREC_FP64));
     return DCSD_OK;

@@ -122,3 +122,17 @@ def test_integer_unit_conversions_match_hardware(P):
     ties, near-ties) must convert exactly as the hardware does."""
     from paper_2401_11935_gb300 import _lib
     assert _lib.dcsd_selftest_conversions() == 0
+
+
+def test_mixed_solve_matches_fp64_c2(P):
+    """The mixed-precision solve (BF16, BF16X6, FP64 polish) reaches the FP64
+    solution: singlet and triplet energies within 1e-6 Eh (here far below)."""
+    s = make_system("c2")
+    eng = P.Engine.from_system(s)
+    _, f = eng.solve(method=1, precision=P.PREC_FP64, tol=1e-8, maxiter=80)
+    _, m = eng.solve(method=1, precision=P.PREC_MIXED, tol=1e-8, maxiter=80)
+    eng.close()
+    assert f.converged and m.converged
+    assert m.switched_at > 0 and m.polished_at > m.switched_at
+    assert abs(m.E_S - f.E_S) < 1e-6 and abs(m.E_T - f.E_T) < 1e-6
+    assert m.seconds < f.seconds
