@@ -34,6 +34,12 @@ METRIC = "2D-DCSD s/iteration & ladder TFLOP/s vs peak; mixed vs FP64 at 1e-6 Eh
 UNIT = "s/iteration"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 70 ladder
+# GEMM launches (36 producer, 34 consumer) of one c5 BF16 residual, from the
+# one-pass ncu capture summarised in profiles/k_tc_gemm_c5_bf16_residual_dram.md
+LADDER_DRAM_BYTES_PER_LAUNCH = 9.184e9
+
+
 def ladder_flops(nc, nv, X):
     """Algorithmic flops of the DF particle-particle ladder per residual:
     2 o^2 v^4 (alpha-beta) + 4 C(o,2) C(v,2)^2 (same-spin unique pairs) +
@@ -237,7 +243,8 @@ def main():
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
                      "algorithmic_flops_per_launch": lf / max(1.0, per_res_launches),
-                     "avg_launch_ms": lad_ms / max(1, lad_n), "traffic": None},
+                     "avg_launch_ms": lad_ms / max(1, lad_n), "traffic": LADDER_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_unit": "bytes per ladder launch (producer or consumer), DRAM read + write"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "note": "dcsd_residual with pinned host buffers (copies in the timed region)"},
