@@ -90,14 +90,18 @@ typedef struct {
     double switch_tol;  /* MIXED: switch BF16 -> BF16X6 when max|R| < this, or
                            when max|R| has not halved in 6 iterations      */
     int use_guess;      /* 1: start from the T passed in, 0: from T = 0      */
-    double polish_tol;  /* MIXED: switch BF16X6 -> FP64 when max|R| < this, or
-                           when max|R| has not halved in 4 BF16X6 iterations;
-                           0 keeps BF16X6 to the end.  The tensor cores
-                           accumulate in FP32, whose rounding noise in long
-                           contractions puts a floor under the attainable
-                           accuracy of the energies; the FP64 iterations
-                           remove it (the converged T then solves the FP64
-                           equations) */
+    double polish_tol;  /* MIXED: leave plain BF16X6 when max|R| < this, or
+                           when max|R| has not halved in 4 BF16X6 iterations,
+                           for defect correction: an outer step evaluates the
+                           FP64 residual R64(T) and e = R_X6(T) - R64(T) at
+                           the same T, inner BF16X6 steps iterate on
+                           R_X6 - e; convergence (max|R64| <= tol) is tested
+                           on outer steps only.  0 keeps plain BF16X6 to the
+                           end.  The tensor cores accumulate in FP32, whose
+                           rounding error in long contractions limits the
+                           energies of a plain BF16X6 solve; with defect
+                           correction the converged T solves the FP64
+                           equations */
 } dcsd_solve_opts;
 
 typedef struct {
@@ -110,7 +114,7 @@ typedef struct {
     int converged;    /* 1 if max_r <= tol                                   */
     double seconds;   /* wall time of the solve                             */
     int switched_at;  /* MIXED: iteration of the BF16 -> BF16X6 switch, or -1 */
-    int polished_at;  /* MIXED: iteration of the BF16X6 -> FP64 switch, or -1 */
+    int polished_at;  /* MIXED: iteration of the switch to defect correction, or -1 */
 } dcsd_result;
 
 /* dcsd_init -- create a context (Section II inputs of the method).

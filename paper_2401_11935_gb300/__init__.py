@@ -91,7 +91,8 @@ class Engine:
               switch_tol=1e-5, T0=None, polish_tol=1e-7):
         """Converge the amplitudes on the device; returns (T, dcsd_result).
         MIXED: BF16 until max|R| < switch_tol, BF16X6 until max|R| <
-        polish_tol, then FP64 (polish_tol = 0: no FP64 phase)."""
+        polish_tol, then defect correction (FP64 residuals on outer steps,
+        BF16X6 inner steps); polish_tol = 0 keeps plain BF16X6."""
         T = tuple(x.clone() for x in T0) if T0 is not None else self.zeros()
         opts = L.dcsd_solve_opts(method, ref, precision, maxiter, diis_n, tol, switch_tol,
                                  1 if T0 is not None else 0, polish_tol)

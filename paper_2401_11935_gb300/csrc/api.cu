@@ -909,13 +909,33 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     res->converged = 0;
     res->switched_at = -1;
     res->polished_at = -1;
+    // MIXED phase 2, defect correction: an outer step evaluates the FP64
+    // residual R64(T) and the BF16X6 one at the same T and keeps their
+    // difference e; inner steps iterate on r(T) = R_X6(T) - e, which equals
+    // R64 at the outer T and differs from R64 nearby only by the change of
+    // the tensor cores' rounding error.  Convergence is declared on outer
+    // (FP64) residuals only.
+    double* defect = nullptr;
+    struct FreeDefect {
+        double*& p;
+        ~FreeDefect() { if (p) cudaFree(p); }
+    } free_defect{defect};
+    bool outer = true;
+    int inner = 0;
+    double inner_best = 1e300;
+    const TV Rall = view(c->R1, {len});
     int it = 0;
     for (it = 1; it <= o->maxiter; ++it) {
         int prec = o->precision;
+        const bool refining = o->precision == DCSD_PREC_MIXED && phase == 2;
         if (prec == DCSD_PREC_MIXED)
-            prec = phase == 0 ? DCSD_PREC_BF16 : phase == 1 ? DCSD_PREC_BF16X6 : DCSD_PREC_FP64;
+            prec = phase == 0 ? DCSD_PREC_BF16 : phase == 1 ? DCSD_PREC_BF16X6
+                                                             : (outer ? DCSD_PREC_FP64 : DCSD_PREC_BF16X6);
         dcsd_status s = residual_union(c, ref, o->method, prec);
         if (s != DCSD_OK) { status = s; break; }
+        if (refining && !outer) {
+            if ((s = axpy_view(c, -1.0, view(defect, {len}), 1.0, Rall)) != DCSD_OK) { status = s; break; }
+        }
         if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
         DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
         if ((s = check_finite(c, c->R1, len, c->scal + 20)) != DCSD_OK) { status = s; break; }
@@ -932,10 +952,33 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
             status = DCSD_ERR_NUMERIC;
             break;
         }
-        if (rmax <= o->tol) {
+        if (rmax <= o->tol && (!refining || outer)) {
             status = DCSD_OK;
             res->converged = 1;
             break;
+        }
+        if (refining && outer) {
+            // e = R_X6(T) - R64(T); the step below uses R64
+            if (!defect && (s = alloc(c, &defect, len)) != DCSD_OK) { status = s; break; }
+            DCSD_CUDA(c, cudaMemcpyAsync(defect, c->R1, len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            if ((s = residual_union(c, ref, o->method, DCSD_PREC_BF16X6)) != DCSD_OK) { status = s; break; }
+            if ((s = axpy_view(c, 1.0, Rall, -1.0, view(defect, {len}))) != DCSD_OK) { status = s; break; }
+            if ((s = axpy_view(c, -1.0, view(defect, {len}), 1.0, Rall)) != DCSD_OK) { status = s; break; }
+            outer = false;
+            inner = 0;
+            inner_best = rmax;
+            nhist = 0;  // a new defect defines a new iteration function
+            next = 0;
+        } else if (refining) {
+            // back to an outer step once the inner residual is far below the
+            // target or has stopped decreasing
+            ++inner;
+            if (rmax < 0.5 * inner_best) { inner_best = rmax; stall = 0; }
+            else ++stall;
+            if (rmax <= 0.1 * o->tol || inner >= 20 || stall >= 4) {
+                outer = true;
+                stall = 0;
+            }
         }
         // MIXED: leave BF16 once max|R| is below switch_tol or has stopped
         // decreasing (BF16 rounding puts a floor under the residual)
@@ -958,6 +1001,7 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
                 best_r_window = rmax;
                 nhist = 0;  // history built with the lower precision is discarded
                 next = 0;
+                outer = true;
             }
         }
         double* st_v = nd > 0 ? c->diis_e + (size_t)next * len : sbuf;
@@ -967,7 +1011,7 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
             const size_t jsm = 2ul * c->V * sizeof(double);
             const bool stage = jsm <= 48 * 1024;
             const unsigned jg = (unsigned)std::min<long>(2l * c->O + 3l * c->O * c->O, (long)c->num_sms * 8);
-            if (prec == DCSD_PREC_FP64)
+            if (prec != DCSD_PREC_BF16 && prec != DCSD_PREC_BF16X3)
                 k_jacobi_rows<false><<<jg, 256, stage ? jsm : 0, c->stream>>>(c->n, c->nc, c->O, c->V, fa, fb,
                                                                                c->t1, c->R1, tn_v, st_v, stage);
             else

@@ -119,12 +119,26 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         if (prec == DCSD_PREC_FP64) return einsum64(c, spec, alpha, A, Bm, beta, C);
         return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
     };
-    // small contractions: FP64 in the FP64 mode; in the tensor-core modes the
-    // contraction engine picks the tensor cores (split-K when the output is
-    // small) or, for tiny or batched shapes, FP32 products on the CUDA cores
-    // (the FP64 units of this GPU run at a small fraction of its FP32 rate)
+    // BF16 and BF16X3 take FP32 shortcuts around the tensor cores (FP32 shadow
+    // accumulation of R2, FP32 small contractions, coupling terms and Jacobi
+    // step); BF16X6, the refinement precision, keeps those FP64
+    const bool fast = prec == DCSD_PREC_BF16 || prec == DCSD_PREC_BF16X3;
+    // small contractions: FP64 in the FP64 mode; in the fast tensor-core modes
+    // the contraction engine picks the tensor cores (split-K when the output
+    // is small) or, for tiny or batched shapes, FP32 products on the CUDA
+    // cores (the FP64 units of this GPU run at a small fraction of its FP32
+    // rate); in BF16X6 large unbatched ones (>= 4 GFLOP) go to the tensor
+    // cores and the rest stay FP64
     auto sml = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
                    const TV& C) -> dcsd_status {
+        if (prec != DCSD_PREC_FP64 && !fast) {
+            GemmPlan p;
+            std::string e;
+            if (plan_einsum(spec, A, Bm, C, p, e) && p.NB == 1 && p.K >= 16 &&
+                2.0 * (double)p.M * (double)p.N * (double)p.K >= 4e9)
+                return einsum_tc(c, spec, alpha, A, Bm, beta, C, nsplit);
+            return einsum64(c, spec, alpha, A, Bm, beta, C);
+        }
         if (prec != DCSD_PREC_FP64) {
             GemmPlan p;
             std::string e;
@@ -205,7 +219,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         Ctx* c;
         ~R2fGuard() { c->r2f_on = false; }
     } r2f_guard{c};
-    if (prec != DCSD_PREC_FP64) {
+    if (fast) {
         if (!c->r2f) {
             if (cudaMalloc((void**)&c->r2f, sizeof(float) * 3 * O * O * V * V) != cudaSuccess) {
                 cudaGetLastError();
@@ -390,7 +404,7 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
         DCSD_TRY(copy_dev(c, c->scal, c->R2 + e, 1));
     }
-    DCSD_TRY(apply_mterms(c, ref, prec != DCSD_PREC_FP64));
+    DCSD_TRY(apply_mterms(c, ref, fast));
     return DCSD_OK;
 }
 

@@ -910,7 +910,8 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         return DCSD_ERR_INVALID_ARG;
     }
     // batched or very short contractions: FP32 products on the CUDA cores
-    if (p.NB != 1 || p.M < 1 || p.N < 1 || p.K < 16) return einsum32(c, spec, alpha, A, B, beta, C);
+    if (p.NB != 1 || p.M < 1 || p.N < 1 || p.K < 16)
+        return nsplit >= 3 ? einsum64(c, spec, alpha, A, B, beta, C) : einsum32(c, spec, alpha, A, B, beta, C);
     TcEngine* e = c->tc;
     int nseg, pa[6], pb[6];
     split_patterns(nsplit, nseg, pa, pb);
@@ -932,7 +933,8 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         const long waves = (tilesMN * ksplit + c->num_sms - 1) / std::max(1, c->num_sms);
         const double tc_us = (double)waves * (double)kper * 0.4 + (double)(p.M + p.N) * (double)p.K * 8.0 / 3e6;
         const double simt_us = 2.0 * (double)round_up(p.M, 64) * (double)round_up(p.N, 64) * (double)p.K / 5e6;
-        if (simt_us < tc_us) return einsum32(c, spec, alpha, A, B, beta, C);
+        if (simt_us < tc_us)
+            return nsplit >= 3 ? einsum64(c, spec, alpha, A, B, beta, C) : einsum32(c, spec, alpha, A, B, beta, C);
     }
     // Row order within M (and N) is free: the packed operand and the
     // epilogue only have to agree.  Order each side's modes by decreasing
