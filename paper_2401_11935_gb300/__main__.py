@@ -4,6 +4,8 @@ for profiler captures of single kernels).
     python -m paper_2401_11935_gb300 residual --dims 30,500,1500 --precision bf16 --repeat 1
     python -m paper_2401_11935_gb300 solve --dims 10,120,360 --precision mixed --maxiter 40
     python -m paper_2401_11935_gb300 compare --dims c3 --tol 1e-8
+    python -m paper_2401_11935_gb300 vjp --dims c4 --repeat 2
+    python -m paper_2401_11935_gb300 lambda --dims c4
 
 compare converges the FP64 and the mixed-precision solves from the same
 guess and prints their energies (Delta E_A, W, singlet and triplet energies,
@@ -27,7 +29,7 @@ PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "mixed": 3, "bf16x6": 4}
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2401_11935_gb300")
-    ap.add_argument("what", choices=["residual", "solve", "compare"])
+    ap.add_argument("what", choices=["residual", "solve", "compare", "vjp", "lambda"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--switch-tol", type=float, default=1e-5)
     ap.add_argument("--polish-tol", type=float, default=1e-7)
@@ -63,6 +65,24 @@ def main(argv=None):
                 torch.cuda.synchronize()
                 print(f"residual {k} dims=({s.n_c},{s.n_v},{s.naux}) precision={a.precision} "
                       f"{time.perf_counter() - t0:.4f} s  W={W:.12g} dEA={dE:.12g}", flush=True)
+        elif a.what == "vjp":
+            Td = eng.to_device(random_amplitudes(s, seed=a.seed, ref=a.ref, scale1=1e-3, scale2=1e-3))
+            Rb = eng.to_device(random_amplitudes(s, seed=a.seed + 1, ref=a.ref))
+            for k in range(a.repeat):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                eng.vjp(Td, Rbar=Rb, Ebar=1.0, Wbar=1.0, ref=a.ref, method=method, want_B=True, want_fock=True)
+                torch.cuda.synchronize()
+                print(f"vjp {k} dims=({s.n_c},{s.n_v},{s.naux}) {time.perf_counter() - t0:.4f} s", flush=True)
+        elif a.what == "lambda":
+            T, res = eng.solve(ref=a.ref, method=method, precision=0, maxiter=a.maxiter, tol=a.tol)
+            for state in (1, -1):
+                _, ga, gb, lr = eng.lambda_solve(T, state=state, method=method, ref=a.ref, tol=a.tol,
+                                                 maxiter=a.maxiter)
+                tr = float(ga.diagonal().sum() + gb.diagonal().sum())
+                print(f"lambda state={state:+d} dims=({s.n_c},{s.n_v},{s.naux}) iters={lr.iters} "
+                      f"converged={lr.converged} max|dL/dT|={lr.max_r:.2e} seconds={lr.seconds:.3f} "
+                      f"trace(gamma)={tr:+.6e}", flush=True)
         elif a.what == "solve":
             _, res = eng.solve(ref=a.ref, method=method, precision=PREC[a.precision], maxiter=a.maxiter,
                                tol=a.tol, switch_tol=a.switch_tol, polish_tol=a.polish_tol)

@@ -44,6 +44,9 @@ def test_density_is_energy_derivative(P, method, state):
     eng.close()
     assert lres.converged and lres.max_r <= 1e-10
     ga, gb = ga.cpu().numpy(), gb.cpu().numpy()
+    # a uniform shift of all orbital energies leaves the correlation energy
+    # unchanged (f enters the residual through commutators), so tr(gamma) = 0
+    assert abs(np.trace(ga) + np.trace(gb)) < 1e-9
     rng = np.random.default_rng(17 + method + state)
     mask = (s.parity[:, None] == s.parity[None, :]).astype(float)
     def sym(x):

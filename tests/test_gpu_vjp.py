@@ -127,3 +127,35 @@ def test_autograd_function_matches_vjp(P):
     eng.close()
     for t, g in zip(Tt, G):
         assert np.abs(t.grad.cpu().numpy() - g).max() < 1e-12 * max(1.0, float(np.abs(g).max()))
+
+
+def test_vjp_c4_matches_gpu_finite_differences(P):
+    """The adjoint workload (12 core + 2 open, 160 virtuals, naux 480), FP64:
+    <T_bar, dT> and <B_bar, dB> against central differences of the GPU
+    residual (fourth-order stencil, step 1e-5 along unit-scale directions)."""
+    import torch
+    s = make_system("c4")
+    T = random_amplitudes(s, seed=61, scale1=0.02, scale2=0.02)
+    rng = np.random.default_rng(12)
+    Rb = [rng.normal(0, 1, t.shape) for t in T]
+    dT = [rng.normal(0, 1, t.shape) for t in T]
+    dT[2], dT[3] = ovjp.antisym(dT[2]), ovjp.antisym(dT[3])
+    dB = _sym(rng.normal(0, 1, s.B.shape))
+    eng = P.Engine.from_system(s)
+    G, Bb, _, _ = _gpu_vjp(P, eng, T, Rb, 0.3, -0.6, 0, 1, want_B=True)
+    eng.close()
+
+    def phi(eT, eB):
+        sp = dataclasses.replace(s, B=s.B + eB * dB)
+        e2 = P.Engine.from_system(sp)
+        R, W, dE = e2.residual(e2.to_device([t + eT * d for t, d in zip(T, dT)]), method=1)
+        torch.cuda.synchronize()
+        v = sum(float((r.cpu().numpy() * rb).sum()) for r, rb in zip(R, Rb)) + 0.3 * dE - 0.6 * W
+        e2.close()
+        return v
+
+    h = 1e-5
+    for kind, gpu in (("T", sum(float((g * d).sum()) for g, d in zip(G, dT))), ("B", float((Bb * dB).sum()))):
+        f = (lambda e: phi(e, 0.0)) if kind == "T" else (lambda e: phi(0.0, e))
+        fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
+        assert abs(gpu - fd) < 1e-6 * max(1.0, abs(fd)), (kind, gpu, fd)
