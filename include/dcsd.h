@@ -214,8 +214,8 @@ typedef enum {
 dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
                          long long* launches);
 
-/* dcsd_vjp -- vector-Jacobian product of the FP64 residual (reverse mode).
- * For the residual R(T) of dcsd_residual (same ref, method) with outputs
+/* dcsd_vjp -- vector-Jacobian product of the residual (reverse mode).
+ * For the residual R(T) of dcsd_residual (same ref, method, precision) with outputs
  * (R1a, R1b, R2aa, R2bb, R2ab, dE_A, W), returns for given cotangents
  * (R_bar, dEA_bar, W_bar) the gradients of
  *     <R_bar, R(T)> + dEA_bar * dE_A(T) + W_bar * W(T)
@@ -232,13 +232,17 @@ dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
  *   B_bar             : out or NULL, [naux][n][n] (both triangles: the
  *                       gradient with respect to the array as stored).
  *   fock_a_bar, fock_b_bar : out or NULL, [n][n].
+ * precision: DCSD_PREC_FP64 (CUDA cores) or a tensor-core precision, in
+ * which the forward and the adjoint contractions run on the tensor cores
+ * with that operand split (the adjoint of a BF16X6 residual is accurate to
+ * its FP32-class accuracy).
  * Pointers are host or device memory according to mem_kind.  The call runs
- * the FP64 residual once while recording its operations and then their
- * adjoints; the particle-particle ladder integrals are rebuilt in the
- * reverse sweep, not stored.  Other intermediates are kept in device memory
+ * the residual once while recording its operations and then their
+ * adjoints; the integrals of the particle-particle ladder and of its T1
+ * correction are rebuilt in the reverse sweep, not stored.  Other intermediates are kept in device memory
  * for the duration of the call (about 25 doubly-sized amplitude arrays).
  * Errors: INVALID_ARG, OOM, CUDA. */
-dcsd_status dcsd_vjp(dcsd_ctx* ctx, int ref, int method, int mem_kind,
+dcsd_status dcsd_vjp(dcsd_ctx* ctx, int ref, int method, int precision, int mem_kind,
                      const double* T1a, const double* T1b, const double* T2aa,
                      const double* T2bb, const double* T2ab,
                      const double* R1a_bar, const double* R1b_bar, const double* R2aa_bar,

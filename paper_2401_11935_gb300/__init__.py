@@ -99,12 +99,15 @@ class Engine:
         res = L.dcsd_solve(self.ctx, opts, MEM_DEVICE, [_ptr(x) for x in T])
         return T, res
 
-    def vjp(self, T, Rbar=None, Ebar=0.0, Wbar=0.0, ref=0, method=DCSD, want_B=False, want_fock=False):
-        """Reverse mode of the FP64 residual (device call).  Returns the
-        gradients of <Rbar, R(T)> + Ebar * dE_A(T) + Wbar * W(T) with respect
-        to the five amplitude arrays, and optionally to the DF factors B
-        [naux, n, n] and the two Fock matrices [n, n]: (Tbar, Bbar, fa_bar,
-        fb_bar), absent ones None."""
+    def vjp(self, T, Rbar=None, Ebar=0.0, Wbar=0.0, ref=0, method=DCSD, want_B=False, want_fock=False,
+            precision=PREC_FP64):
+        """Reverse mode of the residual (device call).  Returns the gradients
+        of <Rbar, R(T)> + Ebar * dE_A(T) + Wbar * W(T) with respect to the
+        five amplitude arrays, and optionally to the DF factors B [naux, n, n]
+        and the two Fock matrices [n, n]: (Tbar, Bbar, fa_bar, fb_bar), absent
+        ones None.  precision PREC_FP64 differentiates on the FP64 CUDA cores;
+        a tensor-core precision runs the ladder and G-pass contractions of
+        both sweeps on the tensor cores with that operand split."""
         t = self.torch
         n = self.n_c + 2 + self.n_v
         Tb = tuple(t.zeros_like(x) for x in T)
@@ -112,7 +115,7 @@ class Engine:
         Bb = t.zeros((self.naux, n, n), dtype=t.float64, device=dev) if want_B else None
         Fa = t.zeros((n, n), dtype=t.float64, device=dev) if want_fock else None
         Fb = t.zeros((n, n), dtype=t.float64, device=dev) if want_fock else None
-        L.dcsd_vjp(self.ctx, ref, method, MEM_DEVICE, [_ptr(x) for x in T],
+        L.dcsd_vjp(self.ctx, ref, method, precision, MEM_DEVICE, [_ptr(x) for x in T],
                    [_ptr(x) for x in Rbar] if Rbar is not None else None, Ebar, Wbar,
                    [_ptr(x) for x in Tb], _ptr(Bb) if Bb is not None else None,
                    _ptr(Fa) if Fa is not None else None, _ptr(Fb) if Fb is not None else None)

@@ -5,6 +5,7 @@ for profiler captures of single kernels).
     python -m paper_2401_11935_gb300 solve --dims 10,120,360 --precision mixed --maxiter 40
     python -m paper_2401_11935_gb300 compare --dims c3 --tol 1e-8
     python -m paper_2401_11935_gb300 vjp --dims c4 --repeat 2
+    python -m paper_2401_11935_gb300 vjp --dims c5 --precision bf16x6
     python -m paper_2401_11935_gb300 lambda --dims c4
 
 compare converges the FP64 and the mixed-precision solves from the same
@@ -12,7 +13,8 @@ guess and prints their energies (Delta E_A, W, singlet and triplet energies,
 gap 2W), the differences and the wall time of each converged solve.
 
 --dims is n_c,n_v,naux (core orbitals, external virtuals, DF functions) or
-one of the named workloads c1..c5.  The inputs come from the seeded
+one of the named workloads c1..c5.  --precision defaults to bf16, except
+for vjp and lambda, which default to fp64.  The inputs come from the seeded
 generator in ``synth``; the residual is evaluated at seeded random
 amplitudes of magnitude 1e-3.  Prints one line per call with the device
 time.
@@ -34,13 +36,15 @@ def main(argv=None):
     ap.add_argument("--switch-tol", type=float, default=1e-5)
     ap.add_argument("--polish-tol", type=float, default=1e-7)
     ap.add_argument("--dims", default="c3")
-    ap.add_argument("--precision", default="bf16", choices=sorted(PREC))
+    ap.add_argument("--precision", default=None, choices=sorted(PREC))
     ap.add_argument("--method", default="dcsd", choices=["ccsd", "dcsd"])
     ap.add_argument("--ref", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--maxiter", type=int, default=60)
     ap.add_argument("--seed", type=int, default=3)
     a = ap.parse_args(argv)
+    if a.precision is None:
+        a.precision = "fp64" if a.what in ("vjp", "lambda") else "bf16"
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -71,9 +75,11 @@ def main(argv=None):
             for k in range(a.repeat):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                eng.vjp(Td, Rbar=Rb, Ebar=1.0, Wbar=1.0, ref=a.ref, method=method, want_B=True, want_fock=True)
+                eng.vjp(Td, Rbar=Rb, Ebar=1.0, Wbar=1.0, ref=a.ref, method=method, want_B=True, want_fock=True,
+                        precision=PREC[a.precision])
                 torch.cuda.synchronize()
-                print(f"vjp {k} dims=({s.n_c},{s.n_v},{s.naux}) {time.perf_counter() - t0:.4f} s", flush=True)
+                print(f"vjp {k} dims=({s.n_c},{s.n_v},{s.naux}) precision={a.precision} "
+                      f"{time.perf_counter() - t0:.4f} s", flush=True)
         elif a.what == "lambda":
             T, res = eng.solve(ref=a.ref, method=method, precision=0, maxiter=a.maxiter, tol=a.tol)
             for state in (1, -1):

@@ -76,7 +76,7 @@ def load():
     lib.dcsd_profile.restype = C.c_int
     lib.dcsd_energy_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10
     lib.dcsd_energy_noalloc.restype = C.c_int
-    lib.dcsd_vjp.argtypes = [P, C.c_int, C.c_int, C.c_int] + [P] * 10 + [C.c_double, C.c_double] + [P] * 8
+    lib.dcsd_vjp.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int] + [P] * 10 + [C.c_double, C.c_double] + [P] * 8
     lib.dcsd_vjp.restype = C.c_int
     lib.dcsd_lambda.argtypes = [P, C.POINTER(dcsd_solve_opts), C.c_int, C.c_int] + [P] * 12 + \
         [C.POINTER(dcsd_result)]
@@ -175,10 +175,10 @@ def dcsd_selftest_conversions(stream=None):
     return n.value
 
 
-def dcsd_vjp(ctx, ref, method, mem_kind, T, Rbar, Ebar, Wbar, Tbar, Bbar=None, Fa=None, Fb=None):
+def dcsd_vjp(ctx, ref, method, precision, mem_kind, T, Rbar, Ebar, Wbar, Tbar, Bbar=None, Fa=None, Fb=None):
     """Raw call; T, Rbar (or None), Tbar: 5 pointers each."""
     Rb = list(Rbar) if Rbar is not None else [None] * 5
-    st = load().dcsd_vjp(ctx, ref, method, mem_kind, *T, *Rb, float(Ebar), float(Wbar), *Tbar, Bbar, Fa, Fb)
+    st = load().dcsd_vjp(ctx, ref, method, precision, mem_kind, *T, *Rb, float(Ebar), float(Wbar), *Tbar, Bbar, Fa, Fb)
     _check(st, ctx)
 
 

@@ -496,11 +496,11 @@ extern "C" dcsd_status dcsd_energy(dcsd_ctx* h, int ref, int method, int mem_kin
 }
 
 namespace dcsd {
-dcsd_status vjp_run(Ctx* c, int ref, int method, const double* const* Td, const double* const* Rb, double Ebar,
-                    double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb);
+dcsd_status vjp_run(Ctx* c, int ref, int method, int prec, const double* const* Td, const double* const* Rb,
+                    double Ebar, double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb);
 }
 
-extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int mem_kind, const double* T1a,
+extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int precision, int mem_kind, const double* T1a,
                                 const double* T1b, const double* T2aa, const double* T2bb, const double* T2ab,
                                 const double* R1a_bar, const double* R1b_bar, const double* R2aa_bar,
                                 const double* R2bb_bar, const double* R2ab_bar, double dEA_bar, double W_bar,
@@ -511,9 +511,9 @@ extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int mem_kind, 
     const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
     const double* Rb[5] = {R1a_bar, R1b_bar, R2aa_bar, R2bb_bar, R2ab_bar};
     double* Tb[5] = {T1a_bar, T1b_bar, T2aa_bar, T2bb_bar, T2ab_bar};
-    if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) ||
+    if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) || !valid_prec(precision) ||
         (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
-        c->err = "invalid ref/method/mem_kind";
+        c->err = "invalid ref/method/precision/mem_kind";
         return DCSD_ERR_INVALID_ARG;
     }
     int nrb = 0;
@@ -530,7 +530,8 @@ extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int mem_kind, 
     }
     const size_t nn = (size_t)c->n * c->n, nB = (size_t)c->X * nn;
     if (mem_kind == DCSD_MEM_DEVICE)
-        return vjp_run(c, ref, method, T, nrb ? Rb : nullptr, dEA_bar, W_bar, Tb, B_bar, fock_a_bar, fock_b_bar);
+        return vjp_run(c, ref, method, precision, T, nrb ? Rb : nullptr, dEA_bar, W_bar, Tb, B_bar, fock_a_bar,
+                       fock_b_bar);
     // host memory: stage through device buffers
     DCSD_TRY(ensure_abi(c));
     std::vector<double*> tmp;
@@ -564,7 +565,7 @@ extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int mem_kind, 
     if (B_bar && !(Bd = dev(nB))) return DCSD_ERR_OOM;
     if (fock_a_bar && !(Fad = dev(nn))) return DCSD_ERR_OOM;
     if (fock_b_bar && !(Fbd = dev(nn))) return DCSD_ERR_OOM;
-    DCSD_TRY(vjp_run(c, ref, method, Td, nrb ? Rd : nullptr, dEA_bar, W_bar, Tbd, Bd, Fad, Fbd));
+    DCSD_TRY(vjp_run(c, ref, method, precision, Td, nrb ? Rd : nullptr, dEA_bar, W_bar, Tbd, Bd, Fad, Fbd));
     for (int k = 0; k < 5; ++k)
         DCSD_CUDA(c, cudaMemcpyAsync(Tb[k], Tbd[k], abi_len(c, k) * sizeof(double), cudaMemcpyDeviceToHost,
                                      c->stream));
@@ -697,7 +698,7 @@ extern "C" dcsd_status dcsd_lambda(dcsd_ctx* h, const dcsd_solve_opts* o, int st
     if (o->use_guess) DCSD_TRY(layout_union(c, ref, 0, lam, lam + n1, Ld));
     // record the residual at T
     DCSD_TRY(unpack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]));
-    DCSD_TRY(vjp_record(c, ref, o->method));
+    DCSD_TRY(vjp_record(c, ref, o->method, DCSD_PREC_FP64));
     struct TapeClear {
         Ctx* c;
         ~TapeClear() { c->tape.clear(); }

@@ -75,7 +75,8 @@ enum TapeOpType {
     OP_ECOMB,    // dE_A from the energy pieces in scal[1..9]
     OP_SWAPVIR,  // t2s = t2 with the virtual pair exchanged
     OP_MTERMS,   // two-determinant coupling terms, iarg[0] = ref
-    OP_LADDER    // R2 += sum_cd t2 (ac|bd), integrals rebuilt in the reverse sweep
+    OP_LADDER,   // R2 += sum_cd t2 (ac|bd), integrals rebuilt in the reverse sweep
+    OP_GPASS     // G = sum_cd t2 (kc|bd), integrals rebuilt in the reverse sweep
 };
 
 struct TapeOp {
@@ -152,6 +153,9 @@ struct Ctx {
     // read.
     float* r2f = nullptr;
     bool r2f_on = false;
+    // operands the tensor-core engine may keep packed between contractions
+    // (pack_cache_set; valid only while their data does not change)
+    const double* pack_cache_src[2] = {};
     double* hostbuf = nullptr;    // pinned host staging for scalars
     int ladder_chunk = 8;         // virtual rows per V build chunk (FP64)
 
@@ -285,13 +289,20 @@ void rec_push(Ctx* c, TapeOp&& op);
 dcsd_status copy_dev(Ctx* c, double* dst, const double* src, size_t n);
 dcsd_status zero_dev(Ctx* c, double* dst, size_t n);
 inline bool recording(const Ctx* c) { return c->rec; }
-// FP64 ladder R2 += sum_cd t2 (ac|bd) (chunked, integrals never stored)
-dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk);
+// ladder R2 += sum_cd t2 (ac|bd) by einsum chunks over a (integrals never
+// stored beyond a chunk); nsplit 0: FP64 CUDA cores, else tensor cores with
+// that many operand splits.  One tape entry while recording.
+dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk,
+                     int nsplit = 0);
+// ladder T1-correction intermediate G[s][ij][k][b] = sum_cd t_s[ij][cd] (kc|bd)
+// (G[3] with t_ab exchanged in (c,d)) by chunks over k; one tape entry
+dcsd_status gpass(Ctx* c, const TV& t2, const TV& Bov, const TV& Bvv, const TV& G, double* chunkbuf, long chunk,
+                  int nsplit = 0);
 void vjp_free(Ctx* c);
 // reverse mode in stages: record the FP64 residual at c->t1/c->t2, then any
 // number of reverse sweeps with union-layout seeds; the gradients of the
 // last sweep are at vjp_t1bar/vjp_t2bar (union layout) and vjp_fbar
-dcsd_status vjp_record(Ctx* c, int ref, int method);
+dcsd_status vjp_record(Ctx* c, int ref, int method, int prec);
 dcsd_status vjp_sweep(Ctx* c, const double* R1bar_u, const double* R2bar_u, double Ebar, double Wbar);
 double* vjp_t1bar(Ctx* c);
 double* vjp_t2bar(Ctx* c);
@@ -317,6 +328,8 @@ dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A,
 
 // pp ladder + its T1 correction on tensor cores (R2 += ladder, G = correction)
 dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G);
+// sources whose packed operands einsum_tc may reuse (NULL: none); clears the cache
+void pack_cache_set(Ctx* c, const double* src0, const double* src1);
 
 // record a CUDA event pair around a launch of class cls when profiling
 inline void prof_begin(Ctx* c, int cls) {

@@ -440,9 +440,10 @@ dcsd_status einsum32(Ctx* c, const char* spec, double alpha, const TV& A, const 
 
 static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
                                double beta, const TV& C, bool fp32) {
-    if (c->rec && !fp32) {
+    if (c->rec) {
         TapeOp op;
         op.type = OP_EINSUM;
+        op.iarg[1] = fp32 ? 1 : 0;  // engine of the adjoint contractions
         op.spec = spec;
         op.alpha = alpha;
         op.beta = beta;

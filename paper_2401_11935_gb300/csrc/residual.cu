@@ -259,23 +259,18 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     // ---- particle-particle ladder (undressed (ac|bd), stacked blocks) --------
     TV G = view(scratch(c, c->G, 4 * O * O * O * V), {4, O, O, O, V});
     TV H = view(scratch(c, c->H, 3 * O * O * O * O), {3, O, O, O, O});
-    if (prec != DCSD_PREC_FP64) {
+    if (prec != DCSD_PREC_FP64 && !c->rec) {
         DCSD_TRY(ladder_tc(c, nsplit, c->R2, G.p));
     } else {
+        // FP64, and every precision while recording for the reverse sweep:
+        // chunked einsums whose integrals the reverse sweep rebuilds
+        const int ns = prec == DCSD_PREC_FP64 ? 0 : nsplit;
         const long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
-        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch));
-    // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with t_ab
-    // transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
-    {
-        long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
-        for (long k0 = 0; k0 < O; k0 += kc) {
-            long nk = std::min(kc, O - k0);
-            TV Ic = view(scratch(c, c->big0, nk * V * V * V), {nk, V, V, V});  // [k][c][b][d]
-            DCSD_TRY(big("Lkc,Lbd->kcbd", 1.0, sub(Bov, 1, k0, nk), Bvv, 0.0, Ic));
-            DCSD_TRY(big("sijcd,kcbd->sijkb", 1.0, t2, Ic, 0.0, sub(sub(G, 0, 0, 3), 3, k0, nk)));
-            DCSD_TRY(big("ijdc,kcbd->ijkb", 1.0, blk(t2, 2), Ic, 0.0, sub(blk(G, 3), 2, k0, nk)));
-        }
-    }
+        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, ns));
+        // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with
+        // t_ab transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
+        const long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
+        DCSD_TRY(gpass(c, t2, Bov, Bvv, G, c->big0, kc, ns));
     }
     DCSD_TRY(big("kmcd,sijcd->sijkm", 1.0, J, t2, 0.0, H));
     for (int b = 0; b < 3; ++b) {

@@ -661,6 +661,8 @@ struct TcEngine {
     long* d_growoff = nullptr;  // [rows] offset of the row's G[blk][i][j] slice
     float* wsk = nullptr;       // split-K partial tiles
     size_t wsk_cap = 0;
+    Buf pc[2];                  // pack cache (see pack_operand)
+    std::string pc_key[2];
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -703,6 +705,8 @@ void tc_free(Ctx* c) {
     if (e->d_rowcode) cudaFree(e->d_rowcode);
     if (e->d_growoff) cudaFree(e->d_growoff);
     if (e->wsk) cudaFree(e->wsk);
+    for (int k = 0; k < 2; ++k)
+        if (e->pc[k].p) cudaFree(e->pc[k].p);
     delete e;
     c->tc = nullptr;
 }
@@ -857,6 +861,48 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
 dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
                            const TV& C, int nsplit);
 
+// Pack one operand into `dflt`, or, when its source is one of the context's
+// pack-cache sources (set by callers that contract the same operand many
+// times with unchanged data), into that source's cache slot unless the slot
+// already holds the same packing.
+static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
+                                const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
+                                const int* pat, Buf& dflt, const __nv_bfloat16*& out, bool cacheable = true) {
+    TcEngine* e = c->tc;
+    int slot = -1;
+    for (int k = 0; k < 2 && cacheable; ++k)
+        if (src && src == c->pack_cache_src[k]) slot = k;
+    if (slot < 0) {
+        DCSD_TRY(ensure(c, dflt, (size_t)rows * nseg * Kp));
+        DCSD_TRY(pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, dflt.p));
+        out = dflt.p;
+        return DCSD_OK;
+    }
+    std::string key = std::to_string((uintptr_t)src) + "|" + std::to_string(nr) + "|" + std::to_string(nk) + "|" +
+                      std::to_string(rows) + "|" + std::to_string(K) + "|" + std::to_string(Kp) + "|" +
+                      std::to_string(nseg);
+    for (int i = 0; i < nr; ++i) key += "|r" + std::to_string(rsz[i]) + ":" + std::to_string(rs[i]);
+    for (int i = 0; i < nk; ++i) key += "|k" + std::to_string(ksz[i]) + ":" + std::to_string(ks[i]);
+    for (int i = 0; i < nseg; ++i) key += "|p" + std::to_string(pat[i]);
+    if (e->pc_key[slot] != key) {
+        e->pc_key[slot].clear();
+        DCSD_TRY(ensure(c, e->pc[slot], (size_t)rows * nseg * Kp));
+        DCSD_TRY(pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, e->pc[slot].p));
+        e->pc_key[slot] = key;
+    }
+    out = e->pc[slot].p;
+    return DCSD_OK;
+}
+
+void pack_cache_set(Ctx* c, const double* src0, const double* src1) {
+    c->pack_cache_src[0] = src0;
+    c->pack_cache_src[1] = src1;
+    if (c->tc) {
+        c->tc->pc_key[0].clear();
+        c->tc->pc_key[1].clear();
+    }
+}
+
 // Segments along K whose products sum to the split product:
 //   nsplit 2: x = h + m;       hh + hm + mh                (3 BF16 products)
 //   nsplit 3: x = h + m + l;   hh + hm + mh + hl + lh + mm (6 BF16 products)
@@ -895,9 +941,26 @@ __global__ void k_tc_splitk_reduce(TcEpi epi, int ksplit, const float* ws) {
 
 dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
                       const TV& C, int nsplit) {
+    const bool rec = c->rec;
+    if (rec) {
+        // one tape entry; the engine's own fallbacks are not recorded again
+        TapeOp op;
+        op.type = OP_EINSUM;
+        op.spec = spec;
+        op.alpha = alpha;
+        op.beta = beta;
+        op.A = A;
+        op.B = B;
+        op.C = C;
+        op.iarg[1] = 2;  // tensor cores
+        op.iarg[2] = nsplit;
+        rec_push(c, std::move(op));
+        c->rec = false;
+    }
     c->cur_spec = spec;
     dcsd_status st = einsum_tc_impl(c, spec, alpha, A, B, beta, C, nsplit);
     c->cur_spec = c->ladder_phase ? "ladder" : "";
+    c->rec = rec;
     return st;
 }
 
@@ -954,7 +1017,8 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
     // m side the operand whose fastest mode has the smaller stride in C.
     const long m_fast = p.nm > 0 ? std::labs(p.m_sc[p.nm - 1]) : (1l << 62);
     const long n_fast = p.nn > 0 ? std::labs(p.n_sc[p.nn - 1]) : (1l << 62);
-    if (n_fast < m_fast) {
+    const bool swapped = n_fast < m_fast;
+    if (swapped) {
         GemmPlan q = p;
         q.nm = p.nn; q.nn = p.nm; q.M = p.N; q.N = p.M;
         for (int i = 0; i < kMaxMode; ++i) {
@@ -963,16 +1027,18 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
             q.k_sa[i] = p.k_sb[i]; q.k_sb[i] = p.k_sa[i];
         }
         p = q;
-        DCSD_TRY(ensure(c, e->pa, (size_t)p.M * Kt));
-        DCSD_TRY(ensure(c, e->pb, (size_t)p.N * Kt));
-        DCSD_TRY(pack(c, B.p, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa, e->pa.p));
-        DCSD_TRY(pack(c, A.p, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb, e->pb.p));
-    } else {
-        DCSD_TRY(ensure(c, e->pa, (size_t)p.M * Kt));
-        DCSD_TRY(ensure(c, e->pb, (size_t)p.N * Kt));
-        DCSD_TRY(pack(c, A.p, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa, e->pa.p));
-        DCSD_TRY(pack(c, B.p, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb, e->pb.p));
     }
+    // the m-side operand is the one whose modes p.m_* describe
+    const double* msrc = swapped ? B.p : A.p;
+    const double* nsrc = swapped ? A.p : B.p;
+    const __nv_bfloat16* Apk = nullptr;
+    const __nv_bfloat16* Bpk = nullptr;
+    DCSD_TRY(pack_operand(c, msrc, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa,
+                          e->pa, Apk));
+    // (an operand contracted with a view of itself keeps only the m side cached:
+    // both sides would otherwise share one slot)
+    DCSD_TRY(pack_operand(c, nsrc, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb,
+                          e->pb, Bpk, nsrc != msrc));
     TcEpi epi;
     std::memset(&epi, 0, sizeof(epi));
     epi.mode = 0;
@@ -993,7 +1059,7 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         epi.n_size[i] = i < p.nn ? p.n_size[i] : 1;
         epi.n_s[i] = i < p.nn ? p.n_sc[i] : 0;
     }
-    if (ksplit <= 1) return gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi);
+    if (ksplit <= 1) return gemm_packed(c, Apk, p.M, Bpk, p.N, Kt, epi);
     // split K: partial tiles, then C (or its FP32 shadow) from their sum
     {
         const int nkt = (int)(Kt / TC_BK), kper = (nkt + ksplit - 1) / ksplit;
@@ -1012,7 +1078,7 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
     red.N = p.N;
     epi.mode = 5;
     epi.C32 = e->wsk;
-    DCSD_TRY(gemm_packed(c, e->pa.p, p.M, e->pb.p, p.N, Kt, epi, ksplit));
+    DCSD_TRY(gemm_packed(c, Apk, p.M, Bpk, p.N, Kt, epi, ksplit));
     if (c->trace) trace_begin(c, "tc-splitk-reduce " + c->cur_spec);
     k_tc_splitk_reduce<<<(unsigned)std::max<long>(1, std::min<long>((p.M * p.N + 255) / 256, (long)c->num_sms * 8)),
                          256, 0, c->stream>>>(red, ksplit, e->wsk);

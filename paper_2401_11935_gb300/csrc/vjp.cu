@@ -83,9 +83,30 @@ dcsd_status zero_dev(Ctx* c, double* dst, size_t n) {
     return DCSD_OK;
 }
 
+// one contraction on the engine of a precision: nsplit 0 FP64 CUDA cores,
+// otherwise tensor cores with nsplit operand splits
+static dcsd_status contract(Ctx* c, int nsplit, const char* spec, double alpha, const TV& A, const TV& B,
+                            double beta, const TV& C) {
+    if (nsplit == 0) return einsum64(c, spec, alpha, A, B, beta, C);
+    return einsum_tc(c, spec, alpha, A, B, beta, C, nsplit);
+}
+
+// keeps the tensor-core packings of two operands that stay unchanged over a
+// loop of contractions (t2 and B_vv in the chunked ladder and G pass)
+struct PackCacheScope {
+    Ctx* c;
+    PackCacheScope(Ctx* c_, int nsplit, const double* s0, const double* s1) : c(nsplit > 0 ? c_ : nullptr) {
+        if (c) pack_cache_set(c, s0, s1);
+    }
+    ~PackCacheScope() {
+        if (c) pack_cache_set(c, nullptr, nullptr);
+    }
+};
+
 // R2[s][ij][a][b] += sum_cd t2[s][ij][c][d] (ac|bd), (ac|bd) = sum_L B_L[a][c] B_L[b][d]
 // built for chunks of `chunk` values of a in `chunkbuf` (chunk * V^3 doubles)
-dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk) {
+dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk,
+                     int nsplit) {
     const long V = c->V;
     if (c->rec) {
         TapeOp op;
@@ -94,16 +115,52 @@ dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* 
         op.B = Bvv;
         op.C = R2;
         op.iarg[0] = (int)chunk;
+        op.iarg[1] = nsplit;
+        rec_push(c, std::move(op));
+    }
+    const bool saved = c->rec;
+    c->rec = false;
+    PackCacheScope pcs(c, nsplit, t2.p, Bvv.p);
+    dcsd_status st = DCSD_OK;
+    for (long a0 = 0; a0 < V && st == DCSD_OK; a0 += chunk) {
+        const long na = std::min(chunk, V - a0);
+        TV Vc = view(chunkbuf, {na, V, V, V});  // [a][c][b][d] = (ac|bd)
+        st = contract(c, nsplit, "Lac,Lbd->acbd", 1.0, sub(Bvv, 1, a0, na), Bvv, 0.0, Vc);
+        if (st == DCSD_OK) st = contract(c, nsplit, "sijcd,acbd->sijab", 1.0, t2, Vc, 1.0, sub(R2, 3, a0, na));
+    }
+    c->rec = saved;
+    return st;
+}
+
+// G[s][i][j][k][b] = sum_cd t2[s][ij][cd] (kc|bd) for s = aa, bb, ab and
+// G[3][i][j][k][b] = sum_cd t2ab[ij][dc] (kc|bd), by chunks of k
+dcsd_status gpass(Ctx* c, const TV& t2, const TV& Bov, const TV& Bvv, const TV& G, double* chunkbuf, long chunk,
+                  int nsplit) {
+    const long O = c->O, V = c->V;
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_GPASS;
+        op.A = t2;
+        op.B = Bov;
+        op.X[0] = Bvv;
+        op.C = G;
+        op.iarg[0] = (int)chunk;
+        op.iarg[1] = nsplit;
         rec_push(c, std::move(op));
     }
     const bool saved = c->rec;
     c->rec = false;
     dcsd_status st = DCSD_OK;
-    for (long a0 = 0; a0 < V && st == DCSD_OK; a0 += chunk) {
-        const long na = std::min(chunk, V - a0);
-        TV Vc = view(chunkbuf, {na, V, V, V});  // [a][c][b][d] = (ac|bd)
-        st = einsum64(c, "Lac,Lbd->acbd", 1.0, sub(Bvv, 1, a0, na), Bvv, 0.0, Vc);
-        if (st == DCSD_OK) st = einsum64(c, "sijcd,acbd->sijab", 1.0, t2, Vc, 1.0, sub(R2, 3, a0, na));
+    const TV t2ab = fix(t2, 0, 2);
+    PackCacheScope pcs(c, nsplit, t2.p, Bvv.p);
+    for (long k0 = 0; k0 < O && st == DCSD_OK; k0 += chunk) {
+        const long nk = std::min(chunk, O - k0);
+        TV Ic = view(chunkbuf, {nk, V, V, V});  // [k][c][b][d] = (kc|bd)
+        st = contract(c, nsplit, "Lkc,Lbd->kcbd", 1.0, sub(Bov, 1, k0, nk), Bvv, 0.0, Ic);
+        if (st == DCSD_OK)
+            st = contract(c, nsplit, "sijcd,kcbd->sijkb", 1.0, t2, Ic, 0.0, sub(sub(G, 0, 0, 3), 3, k0, nk));
+        if (st == DCSD_OK)
+            st = contract(c, nsplit, "ijdc,kcbd->ijkb", 1.0, t2ab, Ic, 0.0, sub(fix(G, 0, 3), 2, k0, nk));
     }
     c->rec = saved;
     return st;
@@ -183,10 +240,13 @@ dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
             if (!adj_view(c, op.C, Cb)) return DCSD_OK;
             std::string sa, sb, sc;
             split_spec(op.spec, sa, sb, sc);
-            if (adj_view(c, op.A, Ab))
-                DCSD_TRY(einsum64(c, (sc + "," + sb + "->" + sa).c_str(), op.alpha, Cb, op.B, 1.0, Ab));
-            if (adj_view(c, op.B, Bb))
-                DCSD_TRY(einsum64(c, (sa + "," + sc + "->" + sb).c_str(), op.alpha, op.A, Cb, 1.0, Bb));
+            auto run = [&](const std::string& sp, const TV& x, const TV& y, const TV& z) -> dcsd_status {
+                if (op.iarg[1] == 1) return einsum32(c, sp.c_str(), op.alpha, x, y, 1.0, z);
+                if (op.iarg[1] == 2) return einsum_tc(c, sp.c_str(), op.alpha, x, y, 1.0, z, op.iarg[2]);
+                return einsum64(c, sp.c_str(), op.alpha, x, y, 1.0, z);
+            };
+            if (adj_view(c, op.A, Ab)) DCSD_TRY(run(sc + "," + sb + "->" + sa, Cb, op.B, Ab));
+            if (adj_view(c, op.B, Bb)) DCSD_TRY(run(sa + "," + sc + "->" + sb, op.A, Cb, Bb));
             return scale_adj(c, Cb, op.beta);
         }
         case OP_AXPY: {
@@ -261,22 +321,56 @@ dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
             TV t2b, Bvvb, R2b;
             if (!adj_view(c, op.C, R2b)) return DCSD_OK;
             const bool want_t = adj_view(c, op.A, t2b), want_B = adj_view(c, op.B, Bvvb);
+            PackCacheScope pcs(c, op.iarg[1], op.A.p, op.B.p);
             for (long a0 = 0; a0 < V; a0 += chunk) {
                 const long na = std::min(chunk, V - a0);
                 TV Vc = view(c->big0, {na, V, V, V});
                 TV R2c = sub(R2b, 3, a0, na);
+                const int ns = op.iarg[1];
                 if (want_t) {
-                    DCSD_TRY(einsum64(c, "Lac,Lbd->acbd", 1.0, sub(op.B, 1, a0, na), op.B, 0.0, Vc));
-                    DCSD_TRY(einsum64(c, "sijab,acbd->sijcd", 1.0, R2c, Vc, 1.0, t2b));
+                    DCSD_TRY(contract(c, ns, "Lac,Lbd->acbd", 1.0, sub(op.B, 1, a0, na), op.B, 0.0, Vc));
+                    DCSD_TRY(contract(c, ns, "sijab,acbd->sijcd", 1.0, R2c, Vc, 1.0, t2b));
                 }
                 if (want_B) {
                     TV Yc = view(c->big1, {na, V, V, V});  // [a][c][b][d]
-                    DCSD_TRY(einsum64(c, "sijcd,sijab->acbd", 1.0, op.A, R2c, 0.0, Yc));
-                    DCSD_TRY(einsum64(c, "acbd,Lbd->Lac", 1.0, Yc, op.B, 1.0, sub(Bvvb, 1, a0, na)));
-                    DCSD_TRY(einsum64(c, "Lac,acbd->Lbd", 1.0, sub(op.B, 1, a0, na), Yc, 1.0, Bvvb));
+                    DCSD_TRY(contract(c, ns, "sijcd,sijab->acbd", 1.0, op.A, R2c, 0.0, Yc));
+                    DCSD_TRY(contract(c, ns, "acbd,Lbd->Lac", 1.0, Yc, op.B, 1.0, sub(Bvvb, 1, a0, na)));
+                    DCSD_TRY(contract(c, ns, "Lac,acbd->Lbd", 1.0, sub(op.B, 1, a0, na), Yc, 1.0, Bvvb));
                 }
             }
             return DCSD_OK;
+        }
+        case OP_GPASS: {
+            // G = t2 . Ic with Ic[k][c][b][d] = (kc|bd) = sum_L Bov_L[k][c] Bvv_L[b][d]
+            const long O = c->O, V = c->V, chunk = op.iarg[0];
+            const int ns = op.iarg[1];
+            TV Gb, t2b, Bovb, Bvvb;
+            if (!adj_view(c, op.C, Gb)) return DCSD_OK;
+            const bool want_t = adj_view(c, op.A, t2b);
+            const bool want_ov = adj_view(c, op.B, Bovb), want_vv = adj_view(c, op.X[0], Bvvb);
+            const TV t2ab = fix(op.A, 0, 2);
+            PackCacheScope pcs(c, ns, op.A.p, op.X[0].p);
+            for (long k0 = 0; k0 < O; k0 += chunk) {
+                const long nk = std::min(chunk, O - k0);
+                TV Ic = view(c->big0, {nk, V, V, V});
+                TV G3 = sub(sub(Gb, 0, 0, 3), 3, k0, nk), G1 = sub(fix(Gb, 0, 3), 2, k0, nk);
+                DCSD_TRY(contract(c, ns, "Lkc,Lbd->kcbd", 1.0, sub(op.B, 1, k0, nk), op.X[0], 0.0, Ic));
+                if (want_t) {
+                    DCSD_TRY(contract(c, ns, "sijkb,kcbd->sijcd", 1.0, G3, Ic, 1.0, t2b));
+                    DCSD_TRY(contract(c, ns, "ijkb,kcbd->ijdc", 1.0, G1, Ic, 1.0, fix(t2b, 0, 2)));
+                }
+                if (want_ov || want_vv) {
+                    TV Ib = view(c->big1, {nk, V, V, V});
+                    DCSD_TRY(contract(c, ns, "sijcd,sijkb->kcbd", 1.0, op.A, G3, 0.0, Ib));
+                    DCSD_TRY(contract(c, ns, "ijdc,ijkb->kcbd", 1.0, t2ab, G1, 1.0, Ib));
+                    if (want_ov)
+                        DCSD_TRY(contract(c, ns, "kcbd,Lbd->Lkc", 1.0, Ib, op.X[0], 1.0, sub(Bovb, 1, k0, nk)));
+                    if (want_vv)
+                        DCSD_TRY(contract(c, ns, "Lkc,kcbd->Lbd", 1.0, sub(op.B, 1, k0, nk), Ib, 1.0, Bvvb));
+                }
+            }
+            // the forward wrote G with beta 0
+            return scale_adj(c, Gb, 0.0);
         }
         default:
             c->err = "reverse mode: unknown tape entry";
@@ -325,7 +419,7 @@ static VjpBufs vjp_layout(Ctx* c, double* base) {
 
 // Record the FP64 residual at the amplitudes already in c->t1/c->t2 and set
 // up the adjoint regions.  On return the tape holds the forward.
-dcsd_status vjp_record(Ctx* c, int ref, int method) {
+dcsd_status vjp_record(Ctx* c, int ref, int method, int prec) {
     const long n = c->n, O = c->O, V = c->V, X = c->X;
     const size_t n1 = 2ul * O * V, n2 = 3ul * O * O * V * V, nn = (size_t)n * n;
     const size_t need = vjp_layout(c, nullptr).total;
@@ -367,7 +461,7 @@ dcsd_status vjp_record(Ctx* c, int ref, int method) {
         ~RecGuard() { c->rec = false; }
     } guard{c};
     dcsd_status st = init_constants(c);
-    if (st == DCSD_OK) st = residual_union(c, ref, method, DCSD_PREC_FP64);
+    if (st == DCSD_OK) st = residual_union(c, ref, method, prec);
     const bool lost = !c->rec;  // an arena allocation failed
     c->rec = false;
     if (st != DCSD_OK) return st;
@@ -404,12 +498,12 @@ double* vjp_fbar(Ctx* c, int spin) { return spin == 0 ? vjp_layout(c, c->vbuf).F
 
 // One VJP.  Td: device ABI amplitudes; Rb: device ABI residual cotangents
 // (NULL = zero); Tb: device ABI outputs; Bb, Fab, Fbb: device outputs or NULL.
-dcsd_status vjp_run(Ctx* c, int ref, int method, const double* const* Td, const double* const* Rb, double Ebar,
-                    double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb) {
+dcsd_status vjp_run(Ctx* c, int ref, int method, int prec, const double* const* Td, const double* const* Rb,
+                    double Ebar, double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb) {
     const long n = c->n, X = c->X;
     const size_t nn = (size_t)n * n;
     DCSD_TRY(unpack_T(c, ref, Td[0], Td[1], Td[2], Td[3], Td[4]));
-    DCSD_TRY(vjp_record(c, ref, method));
+    DCSD_TRY(vjp_record(c, ref, method, prec));
     const VjpBufs v = vjp_layout(c, c->vbuf);
     // the residual seeds in the union layout
     const double* s1 = nullptr;

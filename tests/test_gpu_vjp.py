@@ -159,3 +159,34 @@ def test_vjp_c4_matches_gpu_finite_differences(P):
         f = (lambda e: phi(e, 0.0)) if kind == "T" else (lambda e: phi(0.0, e))
         fd = (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
         assert abs(gpu - fd) < 1e-6 * max(1.0, abs(fd)), (kind, gpu, fd)
+
+
+@pytest.mark.parametrize("prec,rtol", [(4, 2e-4), (2, 2e-3), (1, 5e-2)])
+def test_tensor_core_vjp_matches_fp64(P, prec, rtol):
+    """Reverse mode with the ladder and G-pass contractions of both sweeps on
+    the tensor cores (BF16X6, BF16X3, BF16) against the FP64 reverse mode:
+    projected amplitude gradients and B_bar within rtol of their largest
+    element (the tensor-core products carry the operand-split error of the
+    forward residual, about 1e-5 relative for BF16X6)."""
+    s = make_system((6, 60, 120), seed=7)
+    T = random_amplitudes(s, seed=71, scale1=0.02, scale2=0.02)
+    rng = np.random.default_rng(13)
+    Rb = [rng.normal(0, 1, t.shape) for t in T]
+    eng = P.Engine.from_system(s)
+    import torch
+    Td, Rd = eng.to_device(T), eng.to_device(Rb)
+    out = {}
+    for pr in (0, prec):
+        Tb, Bb, Fa, _ = eng.vjp(Td, Rbar=Rd, Ebar=0.4, Wbar=-0.7, ref=0, method=1, want_B=True, want_fock=True,
+                                precision=pr)
+        torch.cuda.synchronize()
+        out[pr] = ([x.cpu().numpy() for x in Tb], _sym(Bb.cpu().numpy()), _sym(Fa.cpu().numpy()))
+    eng.close()
+    G64, B64, F64 = out[0]
+    G, Bt, Ft = out[prec]
+    scale = max(float(np.abs(g).max()) for g in ovjp.project(G64))
+    for g, g64 in zip(ovjp.project(G), ovjp.project(G64)):
+        assert np.abs(g - g64).max() <= rtol * scale
+    assert np.abs(Bt - B64).max() <= rtol * float(np.abs(B64).max())
+    assert np.abs(Ft - F64).max() <= rtol * float(np.abs(F64).max())
+    assert scale > 1e-2
