@@ -291,13 +291,14 @@ dcsd_status zero_dev(Ctx* c, double* dst, size_t n);
 inline bool recording(const Ctx* c) { return c->rec; }
 // ladder R2 += sum_cd t2 (ac|bd) by einsum chunks over a (integrals never
 // stored beyond a chunk); nsplit 0: FP64 CUDA cores, else tensor cores with
-// that many operand splits.  One tape entry while recording.
+// that many operand splits.  One tape entry while recording; compute false
+// writes only that entry (a caller that produces the values another way).
 dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk,
-                     int nsplit = 0);
+                     int nsplit = 0, bool compute = true);
 // ladder T1-correction intermediate G[s][ij][k][b] = sum_cd t_s[ij][cd] (kc|bd)
 // (G[3] with t_ab exchanged in (c,d)) by chunks over k; one tape entry
 dcsd_status gpass(Ctx* c, const TV& t2, const TV& Bov, const TV& Bvv, const TV& G, double* chunkbuf, long chunk,
-                  int nsplit = 0);
+                  int nsplit = 0, bool compute = true);
 void vjp_free(Ctx* c);
 // reverse mode in stages: record the FP64 residual at c->t1/c->t2, then any
 // number of reverse sweeps with union-layout seeds; the gradients of the
@@ -316,7 +317,13 @@ dcsd_status swap_vir_adjoint(Ctx* c, const double* t2sb, double* t2b);
 // union, the caller zeroes the union buffers first; dir 1: union -> ABI)
 dcsd_status layout_union(Ctx* c, int ref, int dir, double* u1, double* u2, double* const* abi);
 dcsd_status add_fock_hh(Ctx* c, double* Wo, const double* F1, const double* F2);
-dcsd_status init_constants(Ctx* c);
+// J = (kc|ld) and the reference exchange matrices K_ref from B.  While
+// recording it writes only the tape entries (the context already holds these
+// products of the unchanged B); prec selects the engine of J's adjoint.
+dcsd_status init_constants(Ctx* c, int prec = DCSD_PREC_FP64);
+// one OP_EINSUM tape entry (engine 0 FP64, 1 FP32, 2 tensor cores with nsplit)
+void record_einsum(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta, const TV& C,
+                   int engine, int nsplit);
 
 // tensor-core engine (tc_gemm.cu)
 dcsd_status tc_init(Ctx* c);

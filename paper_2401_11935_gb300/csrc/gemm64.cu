@@ -438,20 +438,24 @@ dcsd_status einsum32(Ctx* c, const char* spec, double alpha, const TV& A, const 
     return einsum_simt(c, spec, alpha, A, B, beta, C, true);
 }
 
+void record_einsum(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta, const TV& C,
+                   int engine, int nsplit) {
+    TapeOp op;
+    op.type = OP_EINSUM;
+    op.iarg[1] = engine;  // engine of the adjoint contractions
+    op.iarg[2] = nsplit;
+    op.spec = spec;
+    op.alpha = alpha;
+    op.beta = beta;
+    op.A = A;
+    op.B = B;
+    op.C = C;
+    rec_push(c, std::move(op));
+}
+
 static dcsd_status einsum_simt(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B,
                                double beta, const TV& C, bool fp32) {
-    if (c->rec) {
-        TapeOp op;
-        op.type = OP_EINSUM;
-        op.iarg[1] = fp32 ? 1 : 0;  // engine of the adjoint contractions
-        op.spec = spec;
-        op.alpha = alpha;
-        op.beta = beta;
-        op.A = A;
-        op.B = B;
-        op.C = C;
-        rec_push(c, std::move(op));
-    }
+    if (c->rec) record_einsum(c, spec, alpha, A, B, beta, C, fp32 ? 1 : 0, 0);
     GemmArgs g;
     std::string err;
     if (!plan_einsum(spec, A, B, C, g.p, err)) {

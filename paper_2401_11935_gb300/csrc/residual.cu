@@ -32,22 +32,29 @@ TV blk(const TV& v, int b) { return fix(v, 0, b); }
 
 }  // namespace
 
-dcsd_status init_constants(Ctx* c) {
+dcsd_status init_constants(Ctx* c, int prec) {
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
-    DCSD_TRY(einsum64(c, "Lkc,Lld->klcd", 1.0, Bov, Bov, 0.0, view(c->J, {O, O, V, V})));
+    // while recording, J and K_ref already hold these products of the same B
+    const bool rec = c->rec;
+    const int nsplit = prec == DCSD_PREC_BF16X6 ? 3 : prec == DCSD_PREC_BF16X3 ? 2 : 1;
+    auto ein = [&](const char* spec, const TV& A, const TV& Bm, double beta, const TV& C, bool tc) -> dcsd_status {
+        if (!rec) return einsum64(c, spec, 1.0, A, Bm, beta, C);
+        record_einsum(c, spec, 1.0, A, Bm, beta, C, tc ? 2 : 0, tc ? nsplit : 0);
+        return DCSD_OK;
+    };
+    DCSD_TRY(ein("Lkc,Lld->klcd", Bov, Bov, 0.0, view(c->J, {O, O, V, V}), prec != DCSD_PREC_FP64));
     for (int ref = 0; ref < 2; ++ref) {
         Frame f = frame_of(c, ref);
         for (int s = 0; s < 2; ++s) {
             TV K = view(c->Kref[ref][s], {n, n});
             double beta = 0.0;
             if (nc > 0) {
-                DCSD_TRY(einsum64(c, "Lpk,Lkq->pq", 1.0, sub(B, 2, 0, nc), sub(B, 1, 0, nc), 0.0, K));
+                DCSD_TRY(ein("Lpk,Lkq->pq", sub(B, 2, 0, nc), sub(B, 1, 0, nc), 0.0, K, false));
                 beta = 1.0;
             }
-            DCSD_TRY(einsum64(c, "Lp,Lq->pq", 1.0, fix(B, 2, f.occ_act[s]), fix(B, 1, f.occ_act[s]),
-                              beta, K));
+            DCSD_TRY(ein("Lp,Lq->pq", fix(B, 2, f.occ_act[s]), fix(B, 1, f.occ_act[s]), beta, K, false));
         }
     }
     return DCSD_OK;
@@ -259,18 +266,29 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     // ---- particle-particle ladder (undressed (ac|bd), stacked blocks) --------
     TV G = view(scratch(c, c->G, 4 * O * O * O * V), {4, O, O, O, V});
     TV H = view(scratch(c, c->H, 3 * O * O * O * O), {3, O, O, O, O});
-    if (prec != DCSD_PREC_FP64 && !c->rec) {
-        DCSD_TRY(ladder_tc(c, nsplit, c->R2, G.p));
+    if (prec != DCSD_PREC_FP64) {
+        // tensor cores: the fused ladder (integral tiles built on chip) with the
+        // G intermediate; while recording, the tape gets the chunked ladder and
+        // G-pass entries whose integrals the reverse sweep rebuilds
+        const bool rec = c->rec;
+        if (rec) {
+            const long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
+            const long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
+            DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, nsplit, false));
+            DCSD_TRY(gpass(c, t2, Bov, Bvv, G, c->big0, kc, nsplit, false));
+            c->rec = false;
+        }
+        const dcsd_status st = ladder_tc(c, nsplit, c->R2, G.p);
+        c->rec = rec;
+        DCSD_TRY(st);
     } else {
-        // FP64, and every precision while recording for the reverse sweep:
-        // chunked einsums whose integrals the reverse sweep rebuilds
-        const int ns = prec == DCSD_PREC_FP64 ? 0 : nsplit;
+        // FP64: chunked einsums (while recording, one tape entry each)
         const long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
-        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, ns));
+        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, 0));
         // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with
         // t_ab transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
         const long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));
-        DCSD_TRY(gpass(c, t2, Bov, Bvv, G, c->big0, kc, ns));
+        DCSD_TRY(gpass(c, t2, Bov, Bvv, G, c->big0, kc, 0));
     }
     DCSD_TRY(big("kmcd,sijcd->sijkm", 1.0, J, t2, 0.0, H));
     for (int b = 0; b < 3; ++b) {

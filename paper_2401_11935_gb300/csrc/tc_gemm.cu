@@ -661,8 +661,11 @@ struct TcEngine {
     long* d_growoff = nullptr;  // [rows] offset of the row's G[blk][i][j] slice
     float* wsk = nullptr;       // split-K partial tiles
     size_t wsk_cap = 0;
-    Buf pc[2];                  // pack cache (see pack_operand)
-    std::string pc_key[2];
+    static constexpr int kPackSlots = 4;
+    Buf pc[kPackSlots];         // pack cache (see pack_operand)
+    std::string pc_key[kPackSlots];
+    long pc_tick[kPackSlots] = {};
+    long pc_clock = 0;
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -705,8 +708,8 @@ void tc_free(Ctx* c) {
     if (e->d_rowcode) cudaFree(e->d_rowcode);
     if (e->d_growoff) cudaFree(e->d_growoff);
     if (e->wsk) cudaFree(e->wsk);
-    for (int k = 0; k < 2; ++k)
-        if (e->pc[k].p) cudaFree(e->pc[k].p);
+    for (auto& b : e->pc)
+        if (b.p) cudaFree(b.p);
     delete e;
     c->tc = nullptr;
 }
@@ -862,17 +865,19 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
                            const TV& C, int nsplit);
 
 // Pack one operand into `dflt`, or, when its source is one of the context's
-// pack-cache sources (set by callers that contract the same operand many
-// times with unchanged data), into that source's cache slot unless the slot
-// already holds the same packing.
+// pack-cache sources (set by callers that contract the same operands many
+// times with unchanged data), reuse a cache slot holding the same packing
+// (same source, modes, strides and split pattern) or repack into the least
+// recently used slot.  The slot used by the other operand of the current
+// contraction is the most recently used one, so it is never the one evicted.
 static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
                                 const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
-                                const int* pat, Buf& dflt, const __nv_bfloat16*& out, bool cacheable = true) {
+                                const int* pat, Buf& dflt, const __nv_bfloat16*& out) {
     TcEngine* e = c->tc;
-    int slot = -1;
-    for (int k = 0; k < 2 && cacheable; ++k)
-        if (src && src == c->pack_cache_src[k]) slot = k;
-    if (slot < 0) {
+    bool cached = false;
+    for (int k = 0; k < 2; ++k)
+        if (src && src == c->pack_cache_src[k]) cached = true;
+    if (!cached) {
         DCSD_TRY(ensure(c, dflt, (size_t)rows * nseg * Kp));
         DCSD_TRY(pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, dflt.p));
         out = dflt.p;
@@ -884,12 +889,19 @@ static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* r
     for (int i = 0; i < nr; ++i) key += "|r" + std::to_string(rsz[i]) + ":" + std::to_string(rs[i]);
     for (int i = 0; i < nk; ++i) key += "|k" + std::to_string(ksz[i]) + ":" + std::to_string(ks[i]);
     for (int i = 0; i < nseg; ++i) key += "|p" + std::to_string(pat[i]);
-    if (e->pc_key[slot] != key) {
+    int slot = -1;
+    for (int k = 0; k < TcEngine::kPackSlots; ++k)
+        if (e->pc_key[k] == key) slot = k;
+    if (slot < 0) {
+        slot = 0;
+        for (int k = 1; k < TcEngine::kPackSlots; ++k)
+            if (e->pc_tick[k] < e->pc_tick[slot]) slot = k;
         e->pc_key[slot].clear();
         DCSD_TRY(ensure(c, e->pc[slot], (size_t)rows * nseg * Kp));
         DCSD_TRY(pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, e->pc[slot].p));
         e->pc_key[slot] = key;
     }
+    e->pc_tick[slot] = ++e->pc_clock;
     out = e->pc[slot].p;
     return DCSD_OK;
 }
@@ -897,9 +909,16 @@ static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* r
 void pack_cache_set(Ctx* c, const double* src0, const double* src1) {
     c->pack_cache_src[0] = src0;
     c->pack_cache_src[1] = src1;
-    if (c->tc) {
-        c->tc->pc_key[0].clear();
-        c->tc->pc_key[1].clear();
+    if (!c->tc) return;
+    TcEngine* e = c->tc;
+    for (int k = 0; k < TcEngine::kPackSlots; ++k) {
+        e->pc_key[k].clear();
+        e->pc_tick[k] = 0;
+        // the slots hold up to a few GB each: released when the cache is cleared
+        if (!src0 && !src1 && e->pc[k].p) {
+            cudaFree(e->pc[k].p);
+            e->pc[k] = Buf();
+        }
     }
 }
 
@@ -944,17 +963,7 @@ dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A, const
     const bool rec = c->rec;
     if (rec) {
         // one tape entry; the engine's own fallbacks are not recorded again
-        TapeOp op;
-        op.type = OP_EINSUM;
-        op.spec = spec;
-        op.alpha = alpha;
-        op.beta = beta;
-        op.A = A;
-        op.B = B;
-        op.C = C;
-        op.iarg[1] = 2;  // tensor cores
-        op.iarg[2] = nsplit;
-        rec_push(c, std::move(op));
+        record_einsum(c, spec, alpha, A, B, beta, C, 2, nsplit);
         c->rec = false;
     }
     c->cur_spec = spec;
@@ -1035,10 +1044,8 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
     const __nv_bfloat16* Bpk = nullptr;
     DCSD_TRY(pack_operand(c, msrc, p.nm, p.m_size, p.m_sa, p.nk, p.k_size, p.k_sa, p.M, p.K, Kp, nseg, pa,
                           e->pa, Apk));
-    // (an operand contracted with a view of itself keeps only the m side cached:
-    // both sides would otherwise share one slot)
     DCSD_TRY(pack_operand(c, nsrc, p.nn, p.n_size, p.n_sb, p.nk, p.k_size, p.k_sb, p.N, p.K, Kp, nseg, pb,
-                          e->pb, Bpk, nsrc != msrc));
+                          e->pb, Bpk));
     TcEpi epi;
     std::memset(&epi, 0, sizeof(epi));
     epi.mode = 0;

@@ -106,7 +106,7 @@ struct PackCacheScope {
 // R2[s][ij][a][b] += sum_cd t2[s][ij][c][d] (ac|bd), (ac|bd) = sum_L B_L[a][c] B_L[b][d]
 // built for chunks of `chunk` values of a in `chunkbuf` (chunk * V^3 doubles)
 dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* chunkbuf, long chunk,
-                     int nsplit) {
+                     int nsplit, bool compute) {
     const long V = c->V;
     if (c->rec) {
         TapeOp op;
@@ -118,6 +118,7 @@ dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* 
         op.iarg[1] = nsplit;
         rec_push(c, std::move(op));
     }
+    if (!compute) return DCSD_OK;
     const bool saved = c->rec;
     c->rec = false;
     PackCacheScope pcs(c, nsplit, t2.p, Bvv.p);
@@ -135,7 +136,7 @@ dcsd_status ladder64(Ctx* c, const TV& t2, const TV& Bvv, const TV& R2, double* 
 // G[s][i][j][k][b] = sum_cd t2[s][ij][cd] (kc|bd) for s = aa, bb, ab and
 // G[3][i][j][k][b] = sum_cd t2ab[ij][dc] (kc|bd), by chunks of k
 dcsd_status gpass(Ctx* c, const TV& t2, const TV& Bov, const TV& Bvv, const TV& G, double* chunkbuf, long chunk,
-                  int nsplit) {
+                  int nsplit, bool compute) {
     const long O = c->O, V = c->V;
     if (c->rec) {
         TapeOp op;
@@ -148,6 +149,7 @@ dcsd_status gpass(Ctx* c, const TV& t2, const TV& Bov, const TV& Bvv, const TV& 
         op.iarg[1] = nsplit;
         rec_push(c, std::move(op));
     }
+    if (!compute) return DCSD_OK;
     const bool saved = c->rec;
     c->rec = false;
     dcsd_status st = DCSD_OK;
@@ -332,9 +334,19 @@ dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
                     DCSD_TRY(contract(c, ns, "sijab,acbd->sijcd", 1.0, R2c, Vc, 1.0, t2b));
                 }
                 if (want_B) {
+                    // Y[a][c][b][d] = sum_sij t2[sij][cd] R2_bar[sij][ab] as a matrix over the
+                    // pairs (ac), (bd); B_bar_L = B_L (Y + Y^T).  FP64 takes the two products
+                    // B_L Y and B_L Y^T from the chunk rows of Y (fewer operations); the
+                    // tensor cores form the rows of S = Y + Y^T instead (one long-K product
+                    // less, and every product keeps a large output)
                     TV Yc = view(c->big1, {na, V, V, V});  // [a][c][b][d]
                     DCSD_TRY(contract(c, ns, "sijcd,sijab->acbd", 1.0, op.A, R2c, 0.0, Yc));
-                    DCSD_TRY(contract(c, ns, "acbd,Lbd->Lac", 1.0, Yc, op.B, 1.0, sub(Bvvb, 1, a0, na)));
+                    if (ns == 0) {
+                        DCSD_TRY(contract(c, ns, "acbd,Lbd->Lac", 1.0, Yc, op.B, 1.0, sub(Bvvb, 1, a0, na)));
+                    } else {
+                        // Y^T rows: Y[b][d][a][c] = sum_sij t2[sij][dc] R2_bar[sij][ba]
+                        DCSD_TRY(contract(c, ns, "sijdc,sijba->acbd", 1.0, op.A, sub(R2b, 4, a0, na), 1.0, Yc));
+                    }
                     DCSD_TRY(contract(c, ns, "Lac,acbd->Lbd", 1.0, sub(op.B, 1, a0, na), Yc, 1.0, Bvvb));
                 }
             }
@@ -460,7 +472,7 @@ dcsd_status vjp_record(Ctx* c, int ref, int method, int prec) {
         Ctx* c;
         ~RecGuard() { c->rec = false; }
     } guard{c};
-    dcsd_status st = init_constants(c);
+    dcsd_status st = init_constants(c, prec);
     if (st == DCSD_OK) st = residual_union(c, ref, method, prec);
     const bool lost = !c->rec;  // an arena allocation failed
     c->rec = false;
@@ -488,7 +500,18 @@ dcsd_status vjp_sweep(Ctx* c, const double* R1bar_u, const double* R2bar_u, doub
         DCSD_CUDA(c, cudaMemcpyAsync(v.sb, h, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
     }
-    for (size_t k = c->tape.size(); k-- > 0;) DCSD_TRY(reverse_op(c, c->tape[k]));
+    static const char* const kRevLabel[] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, "rev tau",
+                                            "rev fockhh", "rev ecomb", "rev swap_vir", "rev mterms"};
+    for (size_t k = c->tape.size(); k-- > 0;) {
+        const TapeOp& op = c->tape[k];
+        // adjoint kernels outside the traced primitives (einsum, axpy, dot)
+        const char* label = (size_t)op.type < sizeof(kRevLabel) / sizeof(kRevLabel[0]) ? kRevLabel[op.type]
+                                                                                       : nullptr;
+        if (c->trace && label) trace_begin(c, label);
+        const dcsd_status st = reverse_op(c, op);
+        if (c->trace && label) trace_end(c);
+        DCSD_TRY(st);
+    }
     return DCSD_OK;
 }
 
