@@ -37,6 +37,8 @@ dcsd_status init_constants(Ctx* c, int prec) {
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
     // while recording, J and K_ref already hold these products of the same B
+    // (the tensor-core precisions take the adjoints of the two large products,
+    // J and the core part of K_ref, on the tensor cores)
     const bool rec = c->rec;
     const int nsplit = prec == DCSD_PREC_BF16X6 ? 3 : prec == DCSD_PREC_BF16X3 ? 2 : 1;
     auto ein = [&](const char* spec, const TV& A, const TV& Bm, double beta, const TV& C, bool tc) -> dcsd_status {
@@ -51,7 +53,7 @@ dcsd_status init_constants(Ctx* c, int prec) {
             TV K = view(c->Kref[ref][s], {n, n});
             double beta = 0.0;
             if (nc > 0) {
-                DCSD_TRY(ein("Lpk,Lkq->pq", sub(B, 2, 0, nc), sub(B, 1, 0, nc), 0.0, K, false));
+                DCSD_TRY(ein("Lpk,Lkq->pq", sub(B, 2, 0, nc), sub(B, 1, 0, nc), 0.0, K, prec != DCSD_PREC_FP64));
                 beta = 1.0;
             }
             DCSD_TRY(ein("Lp,Lq->pq", fix(B, 2, f.occ_act[s]), fix(B, 1, f.occ_act[s]), beta, K, false));

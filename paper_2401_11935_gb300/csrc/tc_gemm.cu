@@ -537,6 +537,7 @@ struct PackArgs {
     const double* src;
     __nv_bfloat16* dst;
     long rows, K, Kp;
+    long ldd, segs;  // destination row pitch and segment stride (elements)
     int nseg;
     int pat[6];
     int nr, nk;
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
     __shared__ float tile[TR][TK + 1];
     __shared__ long roff[TR], rdst[TR], koff[TK];
     const long ntr = (a.rows + TR - 1) / TR, ntk = (a.Kp + TK - 1) / TK;
-    const long ldd = (long)a.nseg * a.Kp;
+    const long ldd = a.ldd;
     for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
         // consecutive tiles: along k for k-contiguous sources, along the rows
         // otherwise, so that the blocks in flight read nearby addresses (for
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
                 for (int q = 0; q < 4; ++q)
                     w[q] = (uint32_t)__bfloat16_as_ushort(split_part(v[2 * q], a.pat[sg])) |
                            ((uint32_t)__bfloat16_as_ushort(split_part(v[2 * q + 1], a.pat[sg])) << 16);
-                *(uint4*)(d + (long)sg * a.Kp) = make_uint4(w[0], w[1], w[2], w[3]);
+                *(uint4*)(d + (long)sg * a.segs) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         __syncthreads();
@@ -716,10 +717,13 @@ void tc_free(Ctx* c) {
 
 static long round_up(long x, long m) { return (x + m - 1) / m * m; }
 
+// K-major operand [rows][pitch] (BF16), of which the first kt columns are
+// read (pitch 0: kt); p and pitch * 2 bytes must be 16-byte aligned
 static dcsd_status make_map(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, long rows, long kt,
-                            int box_rows) {
+                            int box_rows, long pitch = 0) {
+    if (pitch == 0) pitch = kt;
     cuuint64_t dims[2] = {(cuuint64_t)kt, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(kt * 2)};
+    cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
     cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = c->tc->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)p, dims, strides, box, es,
@@ -732,11 +736,18 @@ static dcsd_status make_map(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, lo
     return DCSD_OK;
 }
 
+// Packs rows x K (padded to Kp) of a strided FP64 source into nseg BF16
+// split segments.  Element (row r, segment s, k) goes to
+// dst[r * ldd + s * segs + k]; the defaults (ldd = nseg * Kp, segs = Kp) put
+// a row's segments side by side, segs = rows_total * Kp with ldd = Kp keeps
+// each segment a contiguous [rows][Kp] operand.
 static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
                         const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
                         const int* pat, __nv_bfloat16* dst, long rvalid = 1l << 62,
-                        long kvalid = 1l << 62, const long* rtab = nullptr) {
+                        long kvalid = 1l << 62, const long* rtab = nullptr, long ldd = 0, long segs = 0) {
     PackArgs a;
+    a.ldd = ldd > 0 ? ldd : (long)nseg * Kp;
+    a.segs = segs > 0 ? segs : Kp;
     a.rtab = rtab;
     a.rvalid = rvalid;
     a.kvalid = kvalid;
@@ -801,8 +812,10 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
 }
 
 // C = alpha * A_p B_p^T (+ beta C); A_p [M][Ktot], B_p [N][Ktot] packed BF16
+// C (epilogue epi) = A[M][Ktot] . B[N][Ktot]^T; the operands are K-major BF16
+// with row pitch `pitch` elements (0: Ktot)
 static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __nv_bfloat16* Bp, long N,
-                               long Ktot, TcEpi& epi, int ksplit = 1) {
+                               long Ktot, TcEpi& epi, int ksplit = 1, long pitch = 0) {
     TcEngine* e = c->tc;
     if (!e->attr_set) {
         size_t s256 = TC_STAGES * (TC_BM * TC_BK * 2 + 256 * TC_BK * 2) + kStageBytesMode2 + 2048;
@@ -813,8 +826,12 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     }
     const int BN = N >= 256 ? 256 : 128;
     CUtensorMap ma, mb;
-    DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM));
-    DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN));
+    if (pitch != 0 && (pitch < Ktot || pitch % 8 != 0 || ((uintptr_t)Ap | (uintptr_t)Bp) % 16 != 0)) {
+        c->err = "tensor-core GEMM: operand pitch or base not aligned";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM, pitch));
+    DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN, pitch));
     epi.M = M;
     epi.N = N;
     const int nkt = (int)(Ktot / TC_BK);
@@ -1200,20 +1217,23 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
         e->tab_O = O;
         e->tab_V = V;
     }
-    // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d)
+    // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d), segment-major:
+    // segment s is the contiguous operand [rows4][K2p] at s * rows4 * K2p (a row
+    // pitch of K2p keeps a TMA box of rows within few pages for every split)
     DCSD_TRY(ensure(c, e->pt, (size_t)rows4 * K2t));
     {
+        const long ss = rows4 * K2p;
         long rs[1] = {V * V};
         long ksz[2] = {V, Vp}, ks[2] = {V, 1};
         if (P > 0)
             DCSD_TRY(pack(c, c->t2, 0, nullptr, nullptr, 2, ksz, ks, 2 * P, K2, K2p, nseg, pa, e->pt.p, 1l << 62, V,
-                          e->d_pairoff));
+                          e->d_pairoff, K2p, ss));
         long rsz2[1] = {O * O};
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks, O * O, K2, K2p, nseg, pa,
-                      e->pt.p + (size_t)2 * P * K2t, 1l << 62, V));
+                      e->pt.p + (size_t)2 * P * K2p, 1l << 62, V, nullptr, K2p, ss));
         long ks2[2] = {1, V};  // (c,d) -> t_ab[ij][d][c]
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks2, O * O, K2, K2p, nseg, pa,
-                      e->pt.p + (size_t)(2 * P + O * O) * K2t, 1l << 62, V));
+                      e->pt.p + (size_t)(2 * P + O * O) * K2p, 1l << 62, V, nullptr, K2p, ss));
     }
     // B_vv packed as [(b,d)][L], d padded (constant over the chunk loop)
     DCSD_TRY(ensure(c, e->pb, (size_t)K2 * Xt));
@@ -1252,18 +1272,20 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 const double* src = c->B + (pass == 0 ? (nc + r0) * n + nc : r0 * n + nc);
                 DCSD_TRY(pack(c, src, 2, rsz, rs, 1, ksz, ks, nr * V, X, XP, nseg, pa, e->pa.p));
             }
-            // producer: tile (r,c) x (b,d) -> V_p[(r,b)][(c,d)] (BF16, consumer-B layout)
+            // producer: tile (r,c) x (b,d) -> V_p[(r,b)][(c,d)] (BF16, consumer-B layout,
+            // segment-major like the stacked amplitudes)
+            const long vrows = nr * Vb;
             TcEpi pe;
             std::memset(&pe, 0, sizeof(pe));
             pe.mode = 2;
             pe.P = e->pv.p;
             pe.alpha = 1.0;
             pe.nseg = nseg;
-            pe.segstride = K2p;
+            pe.segstride = vrows * K2p;
             for (int i = 0; i < 6; ++i) pe.pat[i] = pb[i];
             pe.V = V;
             pe.Vp = Vp;
-            pe.rowlen = K2t;
+            pe.rowlen = K2p;
             pe.Vb = Vb;
             DCSD_TRY(gemm_packed(c, e->pa.p, nr * V, e->pb.p + (size_t)b0 * Vp * Xt, Vb * Vp, Xt, pe));
             // consumer: rows (s,i,j) x cols (r,b) over (c,d)
@@ -1285,15 +1307,22 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 ce.a0 = r0;
                 ce.OO = O * O;
                 ce.VV = V * V;
-                DCSD_TRY(gemm_packed(c, e->pt.p, rows4, e->pv.p, nr * Vb, K2t, ce));
+                // one launch per split product over its two contiguous segments
+                // (the scatter epilogue adds)
+                for (int sp = 0; sp < nseg; ++sp)
+                    DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce));
             } else {
                 ce.C = G + r0 * V;       // G[s][i][j][k][b], row (s,i,j) at the table's offset
-                ce.beta = 0.0;
                 ce.mrow = e->d_growoff;
                 ce.m_size[0] = rows4; ce.m_s[0] = O * V;
                 ce.n_size[0] = nr; ce.n_s[0] = V;
                 ce.n_size[1] = V;  ce.n_s[1] = 1;
-                DCSD_TRY(gemm_packed(c, e->pt.p, rows4, e->pv.p, nr * V, K2t, ce));
+                for (int sp = 0; sp < nseg; ++sp) {
+                    ce.beta = sp == 0 ? 0.0 : 1.0;
+                    DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce));
+                }
             }
         }
     }
