@@ -34,10 +34,11 @@ METRIC = "2D-DCSD s/iteration & ladder TFLOP/s vs peak; mixed vs FP64 at 1e-6 Eh
 UNIT = "s/iteration"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 70 ladder
-# GEMM launches (36 producer, 34 consumer) of one c5 BF16 residual, from the
-# one-pass ncu capture summarised in profiles/k_tc_gemm_c5_bf16_residual_dram.md
-LADDER_DRAM_BYTES_PER_LAUNCH = 9.184e9
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 72 ladder
+# GEMM launches (36 producer, 34 scatter consumer, 2 G-pass consumer) of one c5
+# BF16 residual, from the one-pass ncu capture summarised in
+# profiles/launches_c5_bf16_iteration.md (K-blocked ladder operands)
+LADDER_DRAM_BYTES_PER_LAUNCH = 7.476e9
 
 
 def ladder_flops(nc, nv, X):

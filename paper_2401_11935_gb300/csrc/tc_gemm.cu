@@ -76,6 +76,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
 }
+// K-blocked operand [k block][row][64]: coordinates (0, row, k block)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -158,6 +166,9 @@ struct TcEpi {
     // mode 2: row m = (r, c) with c < V; column n = (b', d) with d < Vp;
     //         element -> P[(r*Vb + b')*rowlen + c*Vp + d]
     long V, Vp, rowlen, Vb;
+    // mode 2 with kbs > 0: K-blocked destination, element (row R, k) at
+    //         P[(k / 64) * kbs + R * 64 + k % 64] (+ segment * segstride)
+    long kbs;
     // mode 3: ladder consumer scatter; row m = (s, i, j), column n = (r, b')
     //         with a = a0 + r, b = a0 + b' (only b >= a is used):
     //         s = 0,1 (same spin): R[s][ij][a][b] += v, R[s][ij][b][a] -= v
@@ -241,7 +252,7 @@ __device__ __forceinline__ void tile_mn(int mn, int tilesM, int tilesN, int grou
 template <int BN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
-              int nkt, int tilesM, int tilesN, int kper, int group, int* err) {
+              int nkt, int tilesM, int tilesN, int kper, int group, int kblk, int* err) {
     constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
     constexpr uint32_t STAGE = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
@@ -298,8 +309,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     mbar_expect_tx(&full[s], STAGE);
-                    tma_load_2d(smem + s * STAGE, &tmA, &full[s], kt * TC_BK, m0);
-                    tma_load_2d(smem + s * STAGE + A_BYTES, &tmB, &full[s], kt * TC_BK, n0);
+                    if (kblk) {
+                        tma_load_3d(smem + s * STAGE, &tmA, &full[s], 0, m0, kt);
+                        tma_load_3d(smem + s * STAGE + A_BYTES, &tmB, &full[s], 0, n0, kt);
+                    } else {
+                        tma_load_2d(smem + s * STAGE, &tmA, &full[s], kt * TC_BK, m0);
+                        tma_load_2d(smem + s * STAGE + A_BYTES, &tmB, &full[s], kt * TC_BK, n0);
+                    }
                     *issued = g + 1;
                 }
             }
@@ -386,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 uint4* stage = (uint4*)(staging + (warp - 2) * 32 * 64 * 2);
                 const long m = (long)m0 + 32 * q + lane;
                 const long r_of = m / epi.V, c_of = m - r_of * epi.V;
-                const long rowbase = r_of * epi.Vb * epi.rowlen + c_of * epi.Vp;
+                const long rowR = r_of * epi.Vb, colK = c_of * epi.Vp;  // destination row / k of b' = d = 0
                 const float alpha = (float)epi.alpha;
 #pragma unroll 1
                 for (int ch = ch0; ch < ch1; ++ch) {
@@ -413,13 +429,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                         for (int it = 0; it < 4; ++it) {
                             const int rrow = it * 8 + (lane >> 2), piece = lane & 3;
-                            const long base = __shfl_sync(0xffffffffu, rowbase, rrow);
+                            const long bR = __shfl_sync(0xffffffffu, rowR, rrow);
+                            const long bK = __shfl_sync(0xffffffffu, colK, rrow);
                             const long mrow = (long)m0 + 32 * q + rrow;
                             const long np = nst + piece * 8;
                             if (mrow < epi.M && np < epi.N) {
                                 const long b = np / epi.Vp, dd = np - b * epi.Vp;
+                                const long R = bR + b, k = bK + dd;  // k is a multiple of 8
+                                const long off = epi.kbs > 0 ? (k >> 6) * epi.kbs + R * 64 + (k & 63)
+                                                             : R * epi.rowlen + k;
                                 const uint4 val = stage[(sgm & 1) * 128 + rrow * 4 + piece];
-                                *(uint4*)(epi.P + base + b * epi.rowlen + dd + sgm * epi.segstride) = val;
+                                *(uint4*)(epi.P + off + sgm * epi.segstride) = val;
                             }
                         }
                         __syncwarp();
@@ -538,6 +558,7 @@ struct PackArgs {
     __nv_bfloat16* dst;
     long rows, K, Kp;
     long ldd, segs;  // destination row pitch and segment stride (elements)
+    long kbs;        // > 0: K-blocked destination, (r, k) at (k / 64) * kbs + r * 64 + k % 64
     int nseg;
     int pat[6];
     int nr, nk;
@@ -628,7 +649,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = tile[rr][g * 8 + q];
-            __nv_bfloat16* d = a.dst + r * ldd + k0 + g * 8;
+            __nv_bfloat16* d = a.kbs > 0 ? a.dst + (k0 / 64) * a.kbs + r * 64 + g * 8 : a.dst + r * ldd + k0 + g * 8;
             for (int sg = 0; sg < a.nseg; ++sg) {
                 uint32_t w[4];
 #pragma unroll
@@ -740,14 +761,17 @@ static dcsd_status make_map(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, lo
 // split segments.  Element (row r, segment s, k) goes to
 // dst[r * ldd + s * segs + k]; the defaults (ldd = nseg * Kp, segs = Kp) put
 // a row's segments side by side, segs = rows_total * Kp with ldd = Kp keeps
-// each segment a contiguous [rows][Kp] operand.
+// each segment a contiguous [rows][Kp] operand; kbs > 0 (with segs) stores
+// each segment K-blocked, (r, k) at (k / 64) * kbs + r * 64 + k % 64.
 static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, const long* rs, int nk,
                         const long* ksz, const long* ks, long rows, long K, long Kp, int nseg,
                         const int* pat, __nv_bfloat16* dst, long rvalid = 1l << 62,
-                        long kvalid = 1l << 62, const long* rtab = nullptr, long ldd = 0, long segs = 0) {
+                        long kvalid = 1l << 62, const long* rtab = nullptr, long ldd = 0, long segs = 0,
+                        long kbs = 0) {
     PackArgs a;
     a.ldd = ldd > 0 ? ldd : (long)nseg * Kp;
     a.segs = segs > 0 ? segs : Kp;
+    a.kbs = kbs;
     a.rtab = rtab;
     a.rvalid = rvalid;
     a.kvalid = kvalid;
@@ -812,10 +836,29 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
 }
 
 // C = alpha * A_p B_p^T (+ beta C); A_p [M][Ktot], B_p [N][Ktot] packed BF16
+// K-blocked operand [kt / 64][rows][64] (BF16): one TMA box of box_rows rows
+// and 64 k is a contiguous block of memory
+static dcsd_status make_map_kblk(Ctx* c, CUtensorMap* map, const __nv_bfloat16* p, long rows, long kt,
+                                 int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)TC_BK, (cuuint64_t)rows, (cuuint64_t)(kt / TC_BK)};
+    cuuint64_t strides[2] = {(cuuint64_t)(TC_BK * 2), (cuuint64_t)(rows * TC_BK * 2)};
+    cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = c->tc->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)p, dims, strides, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->err = "cuTensorMapEncodeTiled (K-blocked) failed (" + std::to_string((int)r) + ")";
+        return DCSD_ERR_CUDA;
+    }
+    return DCSD_OK;
+}
+
 // C (epilogue epi) = A[M][Ktot] . B[N][Ktot]^T; the operands are K-major BF16
-// with row pitch `pitch` elements (0: Ktot)
+// with row pitch `pitch` elements (0: Ktot), or K-blocked (kblocked: both
+// operands [Ktot / 64][rows][64])
 static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __nv_bfloat16* Bp, long N,
-                               long Ktot, TcEpi& epi, int ksplit = 1, long pitch = 0) {
+                               long Ktot, TcEpi& epi, int ksplit = 1, long pitch = 0, bool kblocked = false) {
     TcEngine* e = c->tc;
     if (!e->attr_set) {
         size_t s256 = TC_STAGES * (TC_BM * TC_BK * 2 + 256 * TC_BK * 2) + kStageBytesMode2 + 2048;
@@ -830,8 +873,17 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
         c->err = "tensor-core GEMM: operand pitch or base not aligned";
         return DCSD_ERR_INVALID_ARG;
     }
-    DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM, pitch));
-    DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN, pitch));
+    if (kblocked) {
+        if (Ktot % TC_BK != 0 || ((uintptr_t)Ap | (uintptr_t)Bp) % 16 != 0) {
+            c->err = "tensor-core GEMM: K-blocked operands need K % 64 == 0 and 16-byte aligned bases";
+            return DCSD_ERR_INVALID_ARG;
+        }
+        DCSD_TRY(make_map_kblk(c, &ma, Ap, M, Ktot, TC_BM));
+        DCSD_TRY(make_map_kblk(c, &mb, Bp, N, Ktot, BN));
+    } else {
+        DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM, pitch));
+        DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN, pitch));
+    }
     epi.M = M;
     epi.N = N;
     const int nkt = (int)(Ktot / TC_BK);
@@ -870,9 +922,11 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     }
     ++c->tc_seq;
     if (BN == 256)
-        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group, e->d_err);
+        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group,
+                                                              kblocked ? 1 : 0, e->d_err);
     else
-        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group, e->d_err);
+        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group,
+                                                              kblocked ? 1 : 0, e->d_err);
     trace_end(c);
     prof_end(c, cls);
     return launch_check(c, "tc_gemm");
@@ -1217,23 +1271,23 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
         e->tab_O = O;
         e->tab_V = V;
     }
-    // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d), segment-major:
-    // segment s is the contiguous operand [rows4][K2p] at s * rows4 * K2p (a row
-    // pitch of K2p keeps a TMA box of rows within few pages for every split)
+    // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d): segment s is
+    // the operand at s * rows4 * K2p, stored K-blocked [K2p / 64][rows4][64] so
+    // that each TMA box (64 k x a tile of rows) is one contiguous block
     DCSD_TRY(ensure(c, e->pt, (size_t)rows4 * K2t));
     {
-        const long ss = rows4 * K2p;
+        const long ss = rows4 * K2p, kb = rows4 * 64;
         long rs[1] = {V * V};
         long ksz[2] = {V, Vp}, ks[2] = {V, 1};
         if (P > 0)
             DCSD_TRY(pack(c, c->t2, 0, nullptr, nullptr, 2, ksz, ks, 2 * P, K2, K2p, nseg, pa, e->pt.p, 1l << 62, V,
-                          e->d_pairoff, K2p, ss));
+                          e->d_pairoff, 0, ss, kb));
         long rsz2[1] = {O * O};
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks, O * O, K2, K2p, nseg, pa,
-                      e->pt.p + (size_t)2 * P * K2p, 1l << 62, V, nullptr, K2p, ss));
+                      e->pt.p + (size_t)2 * P * 64, 1l << 62, V, nullptr, 0, ss, kb));
         long ks2[2] = {1, V};  // (c,d) -> t_ab[ij][d][c]
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks2, O * O, K2, K2p, nseg, pa,
-                      e->pt.p + (size_t)(2 * P + O * O) * K2p, 1l << 62, V, nullptr, K2p, ss));
+                      e->pt.p + (size_t)(2 * P + O * O) * 64, 1l << 62, V, nullptr, 0, ss, kb));
     }
     // B_vv packed as [(b,d)][L], d padded (constant over the chunk loop)
     DCSD_TRY(ensure(c, e->pb, (size_t)K2 * Xt));
@@ -1243,7 +1297,15 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
         DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, K2, X, XP, nseg, pb, e->pb.p, V));
     }
     const long chunk = std::max<long>(1, std::min<long>(V, 16));
-    DCSD_TRY(ensure(c, e->pv, (size_t)chunk * V * K2t));
+    {
+        // the producer never writes the K padding [V * Vp, K2p) of a V tile:
+        // a new buffer starts zeroed, so that padding holds zeros or finite
+        // values of earlier tiles (it meets the zero padding of the amplitudes)
+        const __nv_bfloat16* old = e->pv.p;
+        DCSD_TRY(ensure(c, e->pv, (size_t)chunk * V * K2t));
+        if (e->pv.p != old)
+            DCSD_CUDA(c, cudaMemsetAsync(e->pv.p, 0, e->pv.cap * sizeof(__nv_bfloat16), c->stream));
+    }
     DCSD_TRY(ensure(c, e->pa, (size_t)4 * chunk * V * Xt));
     struct PhaseGuard {
         Ctx* c;
@@ -1273,7 +1335,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 DCSD_TRY(pack(c, src, 2, rsz, rs, 1, ksz, ks, nr * V, X, XP, nseg, pa, e->pa.p));
             }
             // producer: tile (r,c) x (b,d) -> V_p[(r,b)][(c,d)] (BF16, consumer-B layout,
-            // segment-major like the stacked amplitudes)
+            // segment-major and K-blocked like the stacked amplitudes)
             const long vrows = nr * Vb;
             TcEpi pe;
             std::memset(&pe, 0, sizeof(pe));
@@ -1286,6 +1348,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
             pe.V = V;
             pe.Vp = Vp;
             pe.rowlen = K2p;
+            pe.kbs = vrows * 64;
             pe.Vb = Vb;
             DCSD_TRY(gemm_packed(c, e->pa.p, nr * V, e->pb.p + (size_t)b0 * Vp * Xt, Vb * Vp, Xt, pe));
             // consumer: rows (s,i,j) x cols (r,b) over (c,d)
@@ -1311,7 +1374,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 // (the scatter epilogue adds)
                 for (int sp = 0; sp < nseg; ++sp)
                     DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
-                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce));
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true));
             } else {
                 ce.C = G + r0 * V;       // G[s][i][j][k][b], row (s,i,j) at the table's offset
                 ce.mrow = e->d_growoff;
@@ -1321,7 +1384,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 for (int sp = 0; sp < nseg; ++sp) {
                     ce.beta = sp == 0 ? 0.0 : 1.0;
                     DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
-                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce));
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true));
                 }
             }
         }
