@@ -183,6 +183,8 @@ struct Ctx {
     std::vector<AdjRegion> regions;
     double* vbuf = nullptr;       // adjoint buffers of the inputs and outputs (vjp.cu)
     size_t vbuf_elems = 0;
+    double* pairbuf = nullptr;    // pair-row stacks of the tensor-core ladder reverse (vjp.cu)
+    size_t pairbuf_elems = 0;
 
     // solver state (device)
     double* diis_t = nullptr;     // [nd][len]

@@ -235,6 +235,130 @@ dcsd_status write_scalar(Ctx* c, double* dev, double v) {
     return DCSD_OK;
 }
 
+// Pair-row stack of a [3][O][O][V][V] array: rows 0..P-1 are the alpha-alpha
+// pairs i < j (row-major), P..2P-1 the beta-beta pairs, then the O*O
+// alpha-beta rows.  antisym: a pair row holds x[s][i][j] - x[s][j][i].
+__device__ __forceinline__ void pair_row_index(long r, long O, long P, long& s, long& i, long& j) {
+    if (r < 2 * P) {
+        s = r / P;
+        long p = r - s * P;
+        i = 0;
+        while (p >= O - 1 - i) {
+            p -= O - 1 - i;
+            ++i;
+        }
+        j = i + 1 + p;
+    } else {
+        s = 2;
+        const long q = r - 2 * P;
+        i = q / O;
+        j = q - i * O;
+    }
+}
+
+__global__ void k_pair_rows(long O, long VV, const double* __restrict__ x, double* __restrict__ y, int antisym) {
+    const long P = O * (O - 1) / 2, R = 2 * P + O * O;
+    for (long r = blockIdx.x; r < R; r += gridDim.x) {
+        long s, i, j;
+        pair_row_index(r, O, P, s, i, j);
+        const double* a = x + ((s * O + i) * O + j) * VV;
+        const double* b = x + ((s * O + j) * O + i) * VV;
+        double* out = y + r * VV;
+        if (antisym && s < 2)
+            for (long e = threadIdx.x; e < VV; e += blockDim.x) out[e] = a[e] - b[e];
+        else
+            for (long e = threadIdx.x; e < VV; e += blockDim.x) out[e] = a[e];
+    }
+}
+
+// x[s][i][j] += y[r] for every stacked row r
+__global__ void k_pair_rows_add(long O, long VV, const double* __restrict__ y, double* __restrict__ x) {
+    const long P = O * (O - 1) / 2, R = 2 * P + O * O;
+    for (long r = blockIdx.x; r < R; r += gridDim.x) {
+        long s, i, j;
+        pair_row_index(r, O, P, s, i, j);
+        double* out = x + ((s * O + i) * O + j) * VV;
+        const double* in = y + r * VV;
+        for (long e = threadIdx.x; e < VV; e += blockDim.x) out[e] += in[e];
+    }
+}
+
+static bool is_amp_layout(const Ctx* c, const TV& v) {
+    const long O = c->O, V = c->V;
+    const long sz[5] = {3, O, O, V, V};
+    if (v.rank != 5) return false;
+    long st = 1;
+    for (int k = 4; k >= 0; --k) {
+        if (v.size[k] != sz[k] || v.stride[k] != st) return false;
+        st *= sz[k];
+    }
+    return true;
+}
+
+// Reverse of the ladder on the tensor cores.  The recorded forward (the fused
+// tensor-core ladder) reads the same-spin amplitudes only at i < j and writes
+// R2[ij] and R2[ji] = -R2[ij] from them, so its adjoint contracts pair rows:
+// t2_bar[ij] += L^T (R2_bar[ij] - R2_bar[ji]) for i < j (nothing for i > j),
+// and Y = sum_ij t2[ij] R2_bar[ij] = sum_{i<j} t2[ij] (R2_bar[ij] - R2_bar[ji]).
+// Returns false (nothing done) when the pair-row buffers cannot be had.
+static bool ladder_reverse_pairs(Ctx* c, const TapeOp& op, const TV& R2b, bool want_t, const TV& t2b, bool want_B,
+                                 const TV& Bvvb, dcsd_status& st) {
+    const long O = c->O, V = c->V, VV = V * V, chunk = op.iarg[0];
+    const int ns = op.iarg[1];
+    if (!is_amp_layout(c, op.A) || !is_amp_layout(c, R2b) || (want_t && !is_amp_layout(c, t2b))) return false;
+    const long Rr = O * (O - 1) + O * O;
+    const size_t need = (size_t)3 * Rr * VV;
+    if (c->pairbuf_elems < need) {
+        if (c->pairbuf) cudaFree(c->pairbuf);
+        c->pairbuf = nullptr;
+        c->pairbuf_elems = 0;
+        if (cudaMalloc((void**)&c->pairbuf, need * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        c->pairbuf_elems = need;
+    }
+    double* Tt = c->pairbuf;            // pair rows of t2
+    double* Rt = Tt + (size_t)Rr * VV;  // antisymmetrised pair rows of R2_bar
+    double* Tb = Rt + (size_t)Rr * VV;  // adjoint of the pair rows of t2
+    const unsigned g = (unsigned)std::max<long>(1, std::min<long>(Rr, (long)c->num_sms * 4));
+    st = DCSD_OK;
+    k_pair_rows<<<g, 256, 0, c->stream>>>(O, VV, R2b.p, Rt, 1);
+    if ((st = launch_check(c, "pair_rows")) != DCSD_OK) return true;
+    if (want_B) {
+        k_pair_rows<<<g, 256, 0, c->stream>>>(O, VV, op.A.p, Tt, 0);
+        if ((st = launch_check(c, "pair_rows")) != DCSD_OK) return true;
+    }
+    if (want_t && cudaMemsetAsync(Tb, 0, (size_t)Rr * VV * sizeof(double), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "reverse mode: cudaMemsetAsync of the pair-row adjoint failed";
+        st = DCSD_ERR_CUDA;
+        return true;
+    }
+    const TV Ttv = view(Tt, {Rr, V, V}), Rtv = view(Rt, {Rr, V, V}), Tbv = view(Tb, {Rr, V, V});
+    PackCacheScope pcs(c, ns, Tt, op.B.p);
+    for (long a0 = 0; a0 < V && st == DCSD_OK; a0 += chunk) {
+        const long na = std::min(chunk, V - a0);
+        if (want_t) {
+            TV Vc = view(c->big0, {na, V, V, V});
+            if ((st = contract(c, ns, "Lac,Lbd->acbd", 1.0, sub(op.B, 1, a0, na), op.B, 0.0, Vc)) != DCSD_OK) break;
+            if ((st = contract(c, ns, "rab,acbd->rcd", 1.0, sub(Rtv, 1, a0, na), Vc, 1.0, Tbv)) != DCSD_OK) break;
+        }
+        if (want_B) {
+            // rows of S = Y + Y^T (see the all-rows form in reverse_op), then B_bar += B S
+            TV Yc = view(c->big1, {na, V, V, V});
+            if ((st = contract(c, ns, "rcd,rab->acbd", 1.0, Ttv, sub(Rtv, 1, a0, na), 0.0, Yc)) != DCSD_OK) break;
+            if ((st = contract(c, ns, "rdc,rba->acbd", 1.0, Ttv, sub(Rtv, 2, a0, na), 1.0, Yc)) != DCSD_OK) break;
+            if ((st = contract(c, ns, "Lac,acbd->Lbd", 1.0, sub(op.B, 1, a0, na), Yc, 1.0, Bvvb)) != DCSD_OK) break;
+        }
+    }
+    if (st == DCSD_OK && want_t) {
+        k_pair_rows_add<<<g, 256, 0, c->stream>>>(O, VV, Tb, t2b.p);
+        st = launch_check(c, "pair_rows_add");
+    }
+    return true;
+}
+
 dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
     TV Ab, Bb, Cb;
     switch (op.type) {
@@ -323,6 +447,10 @@ dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
             TV t2b, Bvvb, R2b;
             if (!adj_view(c, op.C, R2b)) return DCSD_OK;
             const bool want_t = adj_view(c, op.A, t2b), want_B = adj_view(c, op.B, Bvvb);
+            if (op.iarg[1] > 0) {
+                dcsd_status st = DCSD_OK;
+                if (ladder_reverse_pairs(c, op, R2b, want_t, t2b, want_B, Bvvb, st)) return st;
+            }
             PackCacheScope pcs(c, op.iarg[1], op.A.p, op.B.p);
             for (long a0 = 0; a0 < V; a0 += chunk) {
                 const long na = std::min(chunk, V - a0);
@@ -403,6 +531,9 @@ void vjp_free(Ctx* c) {
     if (c->vbuf) cudaFree(c->vbuf);
     c->vbuf = nullptr;
     c->vbuf_elems = 0;
+    if (c->pairbuf) cudaFree(c->pairbuf);
+    c->pairbuf = nullptr;
+    c->pairbuf_elems = 0;
 }
 
 // Adjoint buffers of the inputs and outputs, in the context's vbuf
