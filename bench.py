@@ -98,7 +98,26 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(seconds_budget=20.0):
+def reduce_max(dist, x, device):
+    """Max of a per-rank float over the ranks of the default process group
+    (x itself without one); device: where the reduction tensor lives (cuda
+    for NCCL, cpu for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(t_step, world):
+    """Seconds per iteration of the whole job: N replicas each finish one
+    iteration per step, so the job does N iterations in the max-over-ranks
+    step time t_step."""
+    return t_step / world if world > 1 else t_step
+
+
+def oracle_sample(seconds_budget=20.0, workload=WORKLOAD):
     """Time the CPU oracle (as it stands) on a bounded sample: one 2D-DCSD
     residual of a reduced system with the same structure, scaled to the
     workload by the ratio of o^2 v^4 ladder operation counts."""
@@ -115,7 +134,7 @@ def oracle_sample(seconds_budget=20.0):
         if time.perf_counter() - t0 > seconds_budget or n >= 50:
             break
     dt = (time.perf_counter() - t0) / n
-    c = __import__("synth").CONFIGS[WORKLOAD]
+    c = __import__("synth").CONFIGS[workload]
     scale = ((c[0] + 1) ** 2 * (c[1] + 1) ** 4) / ((nc + 1) ** 2 * (nv + 1) ** 4)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": dt * scale, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -127,12 +146,16 @@ def oracle_sample(seconds_budget=20.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    cb = oracle_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    from synth import CONFIGS
+    nc, nv, X, _, _ = CONFIGS[args.config]
+    cb = oracle_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)), workload=args.config)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_c": 30, "n_open": 2, "n_v": 500, "naux": 1500},
+            "config": {"workload": args.config, "n_c": nc, "n_open": 2, "n_v": nv, "naux": X,
+                       "method": "2D-DCSD", "reference": "A", "precision": "FP64 CPU oracle",
+                       "parallelism": "single process (rank 0)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -193,11 +216,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = L.dcsd_profile(eng.ctx, 0, 0)
     launches = eng.launches() - launches0
-    t_step = ms / 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = reduce_max(dist, ms / 1e3 / args.steps, "cuda")
     # end-to-end: residual through the C ABI with pinned host buffers
     Th = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in T]
     Rh = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in T]
@@ -219,7 +238,7 @@ def main():
     for _ in range(e2e_steps):
         host_residual()
     barrier()
-    e2e = (time.perf_counter() - t0) / e2e_steps
+    e2e = whole_job_value(reduce_max(dist, (time.perf_counter() - t0) / e2e_steps, "cuda"), world)
     nbytes = int(sum(x.numel() * 8 for x in Th))
 
     pk = peaks() or {}
@@ -232,7 +251,7 @@ def main():
     per_res_launches = lad_n / max(1, args.steps)
     achieved = (lf * args.steps) / (lad_ms / 1e3) / 1e12 if lad_ms > 0 else None
     line = {
-        "metric": METRIC, "value": t_step / world if world > 1 else t_step, "unit": UNIT,
+        "metric": METRIC, "value": whole_job_value(t_step, world), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
