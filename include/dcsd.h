@@ -296,6 +296,25 @@ dcsd_status dcsd_lambda(dcsd_ctx* ctx, const dcsd_solve_opts* o, int state, int 
  * Errors: INVALID_ARG (NULL mismatches), NO_DEVICE, OOM, CUDA. */
 dcsd_status dcsd_selftest_conversions(void* stream, long long* mismatches);
 
+/* dcsd_coupling_host -- the two-determinant coupling coefficients
+ * c_q = <Phi_q| exp(T_other) |Phi_other> of the M.W terms (Section II,
+ * Eqs. 3-4: c_ia and c_ijab, with T_other the amplitudes of this frame with
+ * alpha and beta exchanged), evaluated on the host from the same term
+ * tables that the device kernels use (derived by excitation algebra on
+ * occupation strings).  A diagnostic of the table derivation: it needs no
+ * context and no GPU.
+ *   ref        : 0 (Phi_A) or 1 (Phi_B), the frame of the amplitudes and q.
+ *   n_c, n_v   : core orbitals and external virtuals (1..64 external, at
+ *                most 64 core).
+ *   T1a .. T2ab: host arrays, amplitude layout of this header.
+ *   c1a .. c2ab: host arrays (same layouts) receiving c_q.  Same-spin
+ *                elements with i == j or a == b and the A->B element are 0.
+ * Errors: INVALID_ARG (bad ref or sizes, NULL pointer, or a table the
+ * derivation rejects). */
+dcsd_status dcsd_coupling_host(int ref, int n_c, int n_v, const double* T1a, const double* T1b,
+                               const double* T2aa, const double* T2bb, const double* T2ab, double* c1a,
+                               double* c1b, double* c2aa, double* c2bb, double* c2ab);
+
 /* dcsd_energy_noalloc -- Delta E_A (the first term of Eq. 2, as returned by
  * dcsd_energy) for callers that cannot allocate device memory: code that is
  * capturing a CUDA graph, that hands all device memory to its own pool

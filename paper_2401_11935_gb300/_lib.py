@@ -22,7 +22,8 @@ PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
-           "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda"]
+           "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda",
+           "dcsd_coupling_host"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -83,6 +84,8 @@ def load():
     lib.dcsd_lambda.restype = C.c_int
     lib.dcsd_selftest_conversions.argtypes = [P, C.POINTER(C.c_longlong)]
     lib.dcsd_selftest_conversions.restype = C.c_int
+    lib.dcsd_coupling_host.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 10
+    lib.dcsd_coupling_host.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -173,6 +176,19 @@ def dcsd_selftest_conversions(stream=None):
     if st != 0:
         raise DcsdError(st, "dcsd_selftest_conversions failed")
     return n.value
+
+
+def dcsd_coupling_host(ref, n_c, n_v, T):
+    """Coupling coefficients c_q of frame `ref` (host evaluation from the
+    library's term tables); T: five C-contiguous float64 numpy arrays in the
+    amplitude layout.  Returns five arrays in the same layout."""
+    import numpy as np
+    T = [np.ascontiguousarray(x, dtype=np.float64) for x in T]
+    out = [np.zeros_like(x) for x in T]
+    st = load().dcsd_coupling_host(ref, n_c, n_v, *[x.ctypes.data for x in T], *[x.ctypes.data for x in out])
+    if st != 0:
+        raise DcsdError(st, "dcsd_coupling_host failed")
+    return tuple(out)
 
 
 def dcsd_vjp(ctx, ref, method, precision, mem_kind, T, Rbar, Ebar, Wbar, Tbar, Bbar=None, Fa=None, Fb=None):

@@ -1028,3 +1028,96 @@ dcsd_status apply_mterms(Ctx* c, int ref, bool fp32) {
 }
 
 }  // namespace dcsd
+
+// ---------------------------------------------------------------------------
+// host evaluation of the coupling coefficients from the derived tables
+// ---------------------------------------------------------------------------
+extern "C" dcsd_status dcsd_coupling_host(int ref, int n_c, int n_v, const double* T1a, const double* T1b,
+                                          const double* T2aa, const double* T2bb, const double* T2ab, double* c1a,
+                                          double* c1b, double* c2aa, double* c2bb, double* c2ab) {
+    using namespace dcsd;
+    if ((ref != 0 && ref != 1) || n_c < 0 || n_v < 1 || n_c > 64 || n_v > 64 || !T1a || !T1b || !T2aa ||
+        !T2bb || !T2ab || !c1a || !c1b || !c2aa || !c2bb || !c2ab)
+        return DCSD_ERR_INVALID_ARG;
+    Ctx tmp;  // carries the sizes and error text only; no device state
+    tmp.nc = n_c;
+    tmp.nv = n_v;
+    MTables mt;
+    if (derive_tables(&tmp, ref, mt) != DCSD_OK) return DCSD_ERR_INVALID_ARG;
+    const long o = n_c + 1, v = n_v + 1, O = n_c + 2, V = n_v + 2;
+    const Frame f = frame_of(&tmp, ref);
+    // ABI index -> union position (core i < n_c, the spin's active occupied;
+    // the spin's active virtual at a = 0, externals a >= 1 at 2 + a - 1)
+    auto occ = [&](int s, long i) { return i < n_c ? i : (long)f.occ_act[s]; };
+    auto vir = [&](int s, long a) { return a == 0 ? (long)f.vir_act[s] : a + 1; };
+    const long nb = O * O * V * V;
+    std::vector<double> t1(2 * O * V, 0.0), t2(3 * nb, 0.0), t2s(3 * nb, 0.0);
+    const double* T1[2] = {T1a, T1b};
+    const double* T2[3] = {T2aa, T2bb, T2ab};
+    for (int s = 0; s < 2; ++s)
+        for (long i = 0; i < o; ++i)
+            for (long a = 0; a < v; ++a) t1[(s * O + occ(s, i)) * V + vir(s, a)] = T1[s][i * v + a];
+    for (int blk = 0; blk < 3; ++blk) {
+        const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+        for (long i = 0; i < o; ++i)
+            for (long j = 0; j < o; ++j)
+                for (long a = 0; a < v; ++a)
+                    for (long b = 0; b < v; ++b) {
+                        const double x = T2[blk][((i * o + j) * v + a) * v + b];
+                        const long I = occ(s1, i), J = occ(s2, j), A = vir(s1, a), B = vir(s2, b);
+                        t2[blk * nb + ((I * O + J) * V + A) * V + B] = x;
+                        t2s[blk * nb + ((I * O + J) * V + B) * V + A] = x;
+                    }
+    }
+    // one class of q: the sum over its terms of sign x product of factors
+    auto eval = [&](int cls, const long q[4]) {
+        const long pos[8] = {q[0], q[1], q[2], q[3], n_c, n_c + 1, 0, 1};
+        double sum = 0.0;
+        for (int k = 0; k < mt.cnt[cls]; ++k) {
+            const MTerm& m = mt.terms[mt.off[cls] + k];
+            double prod = (double)m.sign;
+            for (int g = 0; g < m.nf; ++g) {
+                const MFac& fa = m.f[g];
+                const long x0 = pos[fa.idx[0]], x1 = pos[fa.idx[1]];
+                if (fa.arr < 2) {
+                    prod *= t1[(fa.arr * O + x0) * V + x1];
+                } else {
+                    const long x2 = pos[fa.idx[2]], x3 = pos[fa.idx[3]];
+                    const std::vector<double>& src = fa.arr < 5 ? t2 : t2s;
+                    prod *= src[(fa.arr < 5 ? fa.arr - 2 : fa.arr - 5) * nb + ((x0 * O + x1) * V + x2) * V + x3];
+                }
+            }
+            sum += prod;
+        }
+        return sum;
+    };
+    double* C1[2] = {c1a, c1b};
+    for (int s = 0; s < 2; ++s)
+        for (long i = 0; i < o; ++i)
+            for (long a = 0; a < v; ++a) {
+                const long I = occ(s, i), A = vir(s, a);
+                const long q[4] = {I, A, 0, 0};
+                C1[s][i * v + a] = eval(48 + s * 4 + ((I == f.occ_act[s]) << 1) + (A == f.vir_act[s]), q);
+            }
+    double* C2[3] = {c2aa, c2bb, c2ab};
+    for (int blk = 0; blk < 3; ++blk) {
+        const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+        for (long i = 0; i < o; ++i)
+            for (long j = 0; j < o; ++j)
+                for (long a = 0; a < v; ++a)
+                    for (long b = 0; b < v; ++b) {
+                        const long I = occ(s1, i), J = occ(s2, j), A = vir(s1, a), B = vir(s2, b);
+                        const bool ai = I == f.occ_act[s1], aj = J == f.occ_act[s2];
+                        const bool aa = A == f.vir_act[s1], ab = B == f.vir_act[s2];
+                        double cv = 0.0;
+                        const bool same_spin_diag = blk != 2 && (i == j || a == b);
+                        const bool a_to_b = blk == 2 && ai && aj && aa && ab;
+                        if (!same_spin_diag && !a_to_b) {
+                            const long q[4] = {I, J, A, B};
+                            cv = eval(blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab, q);
+                        }
+                        C2[blk][((i * o + j) * v + a) * v + b] = cv;
+                    }
+    }
+    return DCSD_OK;
+}
