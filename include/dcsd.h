@@ -315,6 +315,23 @@ dcsd_status dcsd_coupling_host(int ref, int n_c, int n_v, const double* T1a, con
                                const double* T2aa, const double* T2bb, const double* T2ab, double* c1a,
                                double* c1b, double* c2aa, double* c2bb, double* c2ab);
 
+/* dcsd_einsum_host -- C = beta * C + alpha * einsum(spec)(A, B) on the host,
+ * executed from the batched-GEMM plan (batch, row, column and contracted
+ * modes, with adjacent modes merged) that the device contractions of this
+ * library use for the same spec and views.  A diagnostic of the planner: it
+ * needs no context and no GPU.
+ *   spec               : "ab,bc->ac" form, one letter per mode; a letter in
+ *                        A and B but not C is summed; in all three, batched.
+ *   A, B, C            : host arrays (FP64); C is read only if beta != 0.
+ *   rank_x, size_x, stride_x : view of each operand, strides in elements.
+ * Errors: INVALID_ARG (NULL pointer, rank above 8, a spec the planner
+ * rejects: rank or size mismatch, repeated letter in one operand, a letter
+ * summed in one operand only, more than 4 unmergeable modes of one kind). */
+dcsd_status dcsd_einsum_host(const char* spec, double alpha, const double* A, int rank_a,
+                             const long* size_a, const long* stride_a, const double* B, int rank_b,
+                             const long* size_b, const long* stride_b, double beta, double* C, int rank_c,
+                             const long* size_c, const long* stride_c);
+
 /* dcsd_energy_noalloc -- Delta E_A (the first term of Eq. 2, as returned by
  * dcsd_energy) for callers that cannot allocate device memory: code that is
  * capturing a CUDA graph, that hands all device memory to its own pool

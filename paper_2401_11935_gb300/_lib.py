@@ -23,7 +23,7 @@ PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
            "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda",
-           "dcsd_coupling_host"]
+           "dcsd_coupling_host", "dcsd_einsum_host"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -86,6 +86,9 @@ def load():
     lib.dcsd_selftest_conversions.restype = C.c_int
     lib.dcsd_coupling_host.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 10
     lib.dcsd_coupling_host.restype = C.c_int
+    view = [P, C.c_int, P, P]
+    lib.dcsd_einsum_host.argtypes = [C.c_char_p, C.c_double] + view + view + [C.c_double] + view
+    lib.dcsd_einsum_host.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -189,6 +192,28 @@ def dcsd_coupling_host(ref, n_c, n_v, T):
     if st != 0:
         raise DcsdError(st, "dcsd_coupling_host failed")
     return tuple(out)
+
+
+def dcsd_einsum_host(spec, alpha, a, b, beta, c):
+    """c = beta c + alpha einsum(spec)(a, b) executed on the host from the
+    library's contraction plan; a, b, c: float64 numpy arrays or strided
+    views of them (c written in place)."""
+    import numpy as np
+
+    keep = []
+
+    def view(x):
+        if x.dtype != np.float64:
+            raise TypeError("float64 arrays only")
+        n = max(1, x.ndim)
+        sz = (C.c_long * n)(*x.shape)
+        st = (C.c_long * n)(*[s // 8 for s in x.strides])
+        keep.append((sz, st))
+        return [x.__array_interface__["data"][0], x.ndim, C.cast(sz, C.c_void_p), C.cast(st, C.c_void_p)]
+
+    st = load().dcsd_einsum_host(spec.encode(), float(alpha), *view(a), *view(b), float(beta), *view(c))
+    if st != 0:
+        raise DcsdError(st, "dcsd_einsum_host failed for " + spec)
 
 
 def dcsd_vjp(ctx, ref, method, precision, mem_kind, T, Rbar, Ebar, Wbar, Tbar, Bbar=None, Fa=None, Fb=None):

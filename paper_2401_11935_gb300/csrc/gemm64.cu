@@ -1013,3 +1013,59 @@ void trace_report(Ctx* c) {
         fprintf(stderr, "[dcsd trace] %10.3f ms %5ld x  %s\n", a.second.ms, a.second.n, a.first.c_str());
 }
 }  // namespace dcsd
+
+// ---------------------------------------------------------------------------
+// host execution of a contraction plan (diagnostic of the planner)
+// ---------------------------------------------------------------------------
+extern "C" dcsd_status dcsd_einsum_host(const char* spec, double alpha, const double* A, int rank_a,
+                                        const long* size_a, const long* stride_a, const double* B, int rank_b,
+                                        const long* size_b, const long* stride_b, double beta, double* C,
+                                        int rank_c, const long* size_c, const long* stride_c) {
+    using namespace dcsd;
+    if (!spec || !A || !B || !C) return DCSD_ERR_INVALID_ARG;
+    TV t[3];
+    const int rank[3] = {rank_a, rank_b, rank_c};
+    const long* size[3] = {size_a, size_b, size_c};
+    const long* stride[3] = {stride_a, stride_b, stride_c};
+    for (int x = 0; x < 3; ++x) {
+        if (rank[x] < 0 || rank[x] > kMaxRank || (rank[x] > 0 && (!size[x] || !stride[x])))
+            return DCSD_ERR_INVALID_ARG;
+        t[x].rank = rank[x];
+        for (int i = 0; i < rank[x]; ++i) {
+            if (size[x][i] < 0) return DCSD_ERR_INVALID_ARG;
+            t[x].size[i] = size[x][i];
+            t[x].stride[i] = stride[x][i];
+        }
+    }
+    t[0].p = (double*)A;
+    t[1].p = (double*)B;
+    t[2].p = C;
+    GemmPlan P;
+    std::string err;
+    if (!plan_einsum(spec, t[0], t[1], t[2], P, err)) return DCSD_ERR_INVALID_ARG;
+    // offset of linear index idx over n modes (last mode fastest)
+    auto off = [](long idx, int n, const long* sz, const long* s) {
+        long o = 0;
+        for (int j = n - 1; j >= 0; --j) {
+            const long q = idx / sz[j];
+            o += (idx - q * sz[j]) * s[j];
+            idx = q;
+        }
+        return o;
+    };
+    for (long bi = 0; bi < P.NB; ++bi) {
+        const long oa = off(bi, P.nb, P.b_size, P.b_sa), ob = off(bi, P.nb, P.b_size, P.b_sb),
+                   oc = off(bi, P.nb, P.b_size, P.b_sc);
+        for (long m = 0; m < P.M; ++m) {
+            const long am = oa + off(m, P.nm, P.m_size, P.m_sa), cm = oc + off(m, P.nm, P.m_size, P.m_sc);
+            for (long n = 0; n < P.N; ++n) {
+                const long bn = ob + off(n, P.nn, P.n_size, P.n_sb), cn = cm + off(n, P.nn, P.n_size, P.n_sc);
+                double acc = 0.0;
+                for (long k = 0; k < P.K; ++k)
+                    acc += A[am + off(k, P.nk, P.k_size, P.k_sa)] * B[bn + off(k, P.nk, P.k_size, P.k_sb)];
+                C[cn] = beta != 0.0 ? beta * C[cn] + alpha * acc : alpha * acc;
+            }
+        }
+    }
+    return DCSD_OK;
+}
