@@ -12,13 +12,18 @@ What it computes (arXiv 2401.11935, Section II, Eqs. 2-4):
                   (non-diagonal) Fock matrix, written with the textbook
                   Stanton-Gauss intermediates; the energy Delta E_A (Eq. 2);
                   the distinguishable-cluster (DC) modification of the
-                  doubles (the paper applies DC "in the usual way", Sec. II).
+                  doubles (Section II applies DC to the doubles as in
+                  single-reference DCSD).
   * ``twod``   -- the two-determinant layer: the coefficients
                   c_q = <A_q| exp(T_B) |Phi_B> by cluster-to-CI algebra, the
                   coupling W (the residual element of the A->B double),
                   R1 = R^CC - W c1, R2 = R^CC - W (c2 - A(ij;ab)[t1 c1]),
                   masking of the A->B element (Eqs. 3-4 and the text after
                   them).
+  * ``element`` -- single residual elements of the same definitions for
+                  systems of any size (DF integrals contracted on demand);
+                  pinned element by element against ``twod`` on small
+                  systems.
   * ``solve``  -- Jacobi + DIIS iterations and the 2x2 effective Hamiltonian
                   (singlet Delta E_A + W, triplet Delta E_A - W).
   * ``brute``  -- determinant-space brute force (CI vectors, full CI,

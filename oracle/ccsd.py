@@ -91,7 +91,7 @@ def ccsd_residual(fr, t1, t2, a_chunk=16):
 def dc_delta(fr, t2):
     """Distinguishable-cluster modification of the doubles residual.
 
-    Reading (the paper applies DC "in the usual way" to the doubles and
+    Reading (Section II applies DC to the doubles as in single-reference DCSD and
     defers the term list to its DC reference): of the four T2*T2 terms of
     the CCD doubles residual -- the ladder 1/4 <mn||ef> t_ij^ef t_mn^ab, the
     ring 1/2 P(ij)P(ab) <mn||ef> t_im^ae t_jn^bf and the two Fock-like terms

@@ -14,7 +14,7 @@
 // stacked rows of one matrix -- the particle-particle ladder uses one
 // undressed (ac|bd) for all three blocks, plus explicit T1 corrections.
 //
-// DC (Section II: DC applied to the doubles "in the usual way"): the
+// DC (Section II: DC applied to the doubles as in single-reference DCSD): the
 // exchange part of the quadratic ring is dropped (x = 0) and the two
 // Fock-like quadratic terms are halved (y = 1/2); CCSD has x = y = 1.
 #include "common.h"
