@@ -43,3 +43,20 @@ def test_amplitude_slices_match_dense_tensor():
         for _ in range(4):
             sel = tuple(slice(None) if m else int(rng.integers(t2.shape[k])) for k, m in enumerate(mask))
             assert np.array_equal(eo.T.t2(*sel), t2[sel])
+
+
+@pytest.mark.parametrize("ref,method", [(0, 1), (1, 0)])
+def test_sampled_elements_match_full_oracle_c1(ref, method):
+    """The smallest named workload (4 core + 2 open, 20 virtuals, naux 60):
+    sampled elements of every block and W against the full oracle."""
+    s = make_system("c1")
+    T = random_amplitudes(s, seed=70 + ref, ref=ref, scale1=0.05, scale2=0.05)
+    R, W, _ = twod.residual(s, ref, method, T)
+    eo = element.ElementOracle(s, ref, method, T)
+    scale = max(float(np.abs(x).max()) for x in R)
+    assert abs(eo.W() - W) < 1e-13 * max(1.0, abs(W))
+    rng = np.random.default_rng(ref)
+    for blk, x in enumerate(R):
+        for _ in range(8):
+            idx = tuple(int(rng.integers(n)) for n in x.shape)
+            assert abs(element.residual_element(eo, blk, idx) - x[idx]) < 1e-13 * scale, (blk, idx)
