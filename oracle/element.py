@@ -386,6 +386,23 @@ class ElementOracle:
             total += prod
         return s1 * s2 * total
 
+    def energy(self):
+        """Delta E_A = f_ia t_ia + 1/4 <ij||ab> t_ijab + 1/2 <ij||ab> t_ia t_jb (first
+        term of Eq. 2), summed one occupied spin-orbital i at a time."""
+        df, t1, Bov = self.df, self.t1, self.Bov
+        e = float(np.sum(self.f_ov * t1))
+        for i in range(2 * self.o):
+            ti = self.T.t2(i, slice(None), slice(None), slice(None))  # [j,a,b]
+            # sum_jab <ij||ab> t_ijab = sum_jab ((ia|jb) - (ib|ja)) t_ijab
+            direct = np.sum(Bov[:, i, :] * df.mf_e(ti))  # sum_{L,a} B_ia sum_{j,b} t_ijab B_jb
+            exch = np.sum(Bov[:, i, :] * df.me_f(ti))    # sum_{L,b} B_ib sum_{j,a} B_ja t_ijab
+            # sum_jab <ij||ab> t_ia t_jb = sum_L (B_ia t_ia)(B_jb t_jb) - sum_jab (ib|ja) t_ia t_jb
+            P = Bov[:, i, :] @ t1.T                      # [L,j] = sum_b B_ib t_jb
+            Q = df.e(t1[i])                              # [L,j] = sum_a B_ja t_ia
+            tt = (Bov[:, i, :] @ t1[i]) @ self.cL - np.sum(P * Q)
+            e += 0.25 * (direct - exch) + 0.5 * tt
+        return e
+
     def W(self):
         """W: the connected (DC) residual element of the A->B double."""
         if self._W is None:

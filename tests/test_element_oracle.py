@@ -22,10 +22,11 @@ from synth import make_system, random_amplitudes
 def test_every_element_matches_full_oracle(dims, seed, ref, method, z2):
     s = make_system(dims, seed=seed)
     T = random_amplitudes(s, seed=seed + 50, ref=ref, scale1=0.08, scale2=0.08, z2=z2)
-    R, W, _ = twod.residual(s, ref, method, T)
+    R, W, dE = twod.residual(s, ref, method, T)
     eo = element.ElementOracle(s, ref, method, T)
     scale = max(float(np.abs(x).max()) for x in R)
     assert abs(eo.W() - W) < 1e-13 * max(1.0, abs(W))
+    assert abs(eo.energy() - dE) < 1e-14
     for blk, x in enumerate(R):
         for idx in np.ndindex(x.shape):
             assert abs(element.residual_element(eo, blk, idx) - x[idx]) < 1e-13 * scale, (blk, idx)
