@@ -7,7 +7,11 @@ run uses (``python -m paper_2401_11935_gb300 residual --dims <name>``:
 synth.random_amplitudes with seed 3, magnitude 1e-3, reference A), the
 method 2D-DCSD.  Stored: Delta E_A (first term of Eq. 2), W (the A->B
 residual element) and sampled elements of R1a, R1b, R2aa, R2bb, R2ab
-(Eqs. 3-4), at fixed pseudo-random positions.
+(Eqs. 3-4), at fixed pseudo-random positions; and, for the reverse mode, the
+derivative of one R2ab element along a seeded direction d (fourth-order
+central stencil of the element-wise oracle).  Checksums of the generated
+inputs let a consumer detect inputs that differ from these (another numpy
+random stream).
 
 Usage: python tests/golden/make_elements.py c5 [n_samples]
 """
@@ -23,8 +27,27 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from synth import CONFIGS, frame_orbitals, make_system, random_amplitudes  # noqa: E402
 from oracle import element  # noqa: E402
+from oracle.vjp import antisym  # noqa: E402
 
 SEED, SCALE, REF, METHOD = 3, 1e-3, 0, 1
+DIR_SEED, H = 91, 1e-3
+
+
+def direction(T, seed=DIR_SEED):
+    """Random direction over the five amplitude arrays, antisymmetric in the
+    same-spin doubles."""
+    rng = np.random.default_rng(seed)
+    d = [rng.normal(0.0, 1.0, t.shape) for t in T]
+    d[2], d[3] = antisym(d[2]), antisym(d[3])
+    return d
+
+
+def checksums(s, T, d=None):
+    out = {"B": float(s.B.sum()), "fock_a": float(s.fock_a.sum()), "fock_b": float(s.fock_b.sum()),
+           "T": [float(x.sum()) for x in T]}
+    if d is not None:
+        out["d"] = [float(np.abs(x).sum()) for x in d]
+    return out
 
 
 def positions(s, n, rng):
@@ -73,6 +96,17 @@ def main(name, n):
         val = element.residual_element(eo, blk, idx)
         res["elements"].append({"block": blk, "index": list(idx), "value": val})
         print(blk, idx, val, flush=True)
+    # reverse mode: d/de R_q(T + e d) for the first sampled R2ab element
+    q = next(e for e in res["elements"] if e["block"] == 4)
+    d = direction(T)
+
+    def r(e):
+        Te = tuple(t + e * x for t, x in zip(T, d))
+        return element.residual_element(element.ElementOracle(s, REF, METHOD, Te), 4, tuple(q["index"]))
+    deriv = (8.0 * (r(H) - r(-H)) - (r(2 * H) - r(-2 * H))) / (12.0 * H)
+    res["vjp"] = {"block": 4, "index": q["index"], "direction_seed": DIR_SEED, "h": H, "value": deriv}
+    print("vjp directional derivative", deriv, flush=True)
+    res["checksums"] = checksums(s, T, d)
     res["oracle_seconds"] = time.time() - t0
     with open(os.path.join(HERE, f"{name}_elements.json"), "w") as f:
         json.dump(res, f, indent=1)

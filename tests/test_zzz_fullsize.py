@@ -1,18 +1,25 @@
 """Parity at the full size of the large open-shell workload (30 core + 2
 open orbitals, 500 virtuals, naux 1500), in the tensor-core precisions the
-benchmark and the mixed solve use: Delta E_A, W and sampled residual
-elements of the GPU residual against FP64 values of the element-wise oracle
-stored in tests/golden/c5_elements.json (written by
-tests/golden/make_elements.py, which calls only oracle/ and synth/).
-
-Tolerances, as fractions of the largest stored magnitude (W and the sampled
-elements): BF16 2e-2 and BF16X6 2e-3 (measured W deviations: 1.8e-4 and
-1.2e-5 relative); Delta E_A is FP64 in every mode: 1e-12.  Collected last,
-so that its run time (the host builds the c5 inputs) and any failure do not
-hide the other GPU tests."""
+benchmark, the mixed solve and the mixed reverse mode use, against FP64
+values of the element-wise oracle stored in tests/golden/c5_elements.json
+(written by tests/golden/make_elements.py, which calls only oracle/ and
+synth/):
+  * Delta E_A, W and sampled residual elements of the BF16 and BF16X6
+    residuals.  Tolerances, as fractions of the largest stored magnitude:
+    BF16 2e-2, BF16X6 2e-3 (measured W deviations 1.8e-4 and 1.2e-5
+    relative); Delta E_A is FP64 in every mode: 1e-12.
+  * the BF16X6 reverse mode: with a one-hot cotangent at a stored R2ab
+    element q, <T_bar, d> along the stored seeded direction d against the
+    oracle's fourth-order stencil of R_q, to 2e-3 relative.
+The inputs are regenerated here; if their checksums differ from the stored
+ones (another numpy random stream) the tests skip.  Collected last, so that
+their run time (the host builds the c5 inputs) and any failure do not hide
+the other GPU tests."""
+import importlib.util
 import json
 import os
 
+import numpy as np
 import pytest
 
 from synth import make_system, random_amplitudes
@@ -22,6 +29,17 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
+def _golden_module():
+    spec = importlib.util.spec_from_file_location("make_elements", os.path.join(HERE, "golden", "make_elements.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _same(a, b):
+    return abs(a - b) <= 1e-12 * max(1.0, abs(b))
+
+
 @pytest.fixture(scope="module")
 def setup():
     import torch
@@ -29,18 +47,23 @@ def setup():
         pytest.skip("no GPU")
     import paper_2401_11935_gb300 as P
     gold = json.load(open(os.path.join(HERE, "golden", "c5_elements.json")))
+    g = _golden_module()
     s = make_system(gold["workload"])
     amp = gold["amplitudes"]
     T = random_amplitudes(s, seed=amp["seed"], ref=gold["ref"], scale1=amp["scale"], scale2=amp["scale"])
+    cs, ref = g.checksums(s, T), gold["checksums"]
+    if not (all(_same(cs[k], ref[k]) for k in ("B", "fock_a", "fock_b"))
+            and all(_same(x, y) for x, y in zip(cs["T"], ref["T"]))):
+        pytest.skip("regenerated inputs differ from the stored ones (numpy random stream)")
     eng = P.Engine.from_system(s)
     Td = eng.to_device(T)
-    yield P, eng, Td, gold
+    yield P, eng, Td, T, gold, g
     eng.close()
 
 
 @pytest.mark.parametrize("prec,rtol", [(1, 2e-2), (4, 2e-3)])
 def test_c5_sampled_elements_match_oracle(setup, prec, rtol):
-    P, eng, Td, gold = setup
+    P, eng, Td, _, gold, _ = setup
     assert gold["method"] == "2D-DCSD"
     R, W, dE = eng.residual(Td, ref=gold["ref"], method=P.DCSD, precision=prec)
     scale = max([abs(gold["W"])] + [abs(e["value"]) for e in gold["elements"]])
@@ -49,3 +72,20 @@ def test_c5_sampled_elements_match_oracle(setup, prec, rtol):
     for e in gold["elements"]:
         got = float(R[e["block"]][tuple(e["index"])].item())
         assert abs(got - e["value"]) < rtol * scale, (e, got)
+
+
+def test_c5_bf16x6_vjp_matches_oracle(setup):
+    import torch
+    P, eng, Td, T, gold, g = setup
+    v = gold["vjp"]
+    d = g.direction(T, v["direction_seed"])
+    dsum = [float(np.abs(x).sum()) for x in d]
+    if not all(_same(x, y) for x, y in zip(dsum, gold["checksums"]["d"])):
+        pytest.skip("regenerated direction differs from the stored one (numpy random stream)")
+    Rb = [np.zeros_like(t) for t in T]
+    Rb[v["block"]][tuple(v["index"])] = 1.0
+    Tb, _, _, _ = eng.vjp(Td, Rbar=eng.to_device(Rb), Ebar=0.0, Wbar=0.0, ref=gold["ref"], method=P.DCSD,
+                          precision=P.PREC_BF16X6)
+    torch.cuda.synchronize()
+    gpu = sum(float((t.cpu().numpy() * x).sum()) for t, x in zip(Tb, d))
+    assert abs(gpu - v["value"]) < 2e-3 * abs(v["value"]), (gpu, v["value"])
