@@ -37,7 +37,9 @@ def _golden_module():
 
 
 def _same(a, b):
-    return abs(a - b) <= 1e-12 * max(1.0, abs(b))
+    # summation order (SIMD width) may differ between machines: 1e-9 relative;
+    # another random stream changes these sums at the 1e-5 level or more
+    return abs(a - b) <= 1e-9 * max(1e-300, abs(b))
 
 
 @pytest.fixture(scope="module")
