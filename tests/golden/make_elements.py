@@ -43,10 +43,12 @@ def direction(T, seed=DIR_SEED):
 
 
 def checksums(s, T, d=None):
-    out = {"B": float(s.B.sum()), "fock_a": float(s.fock_a.sum()), "fock_b": float(s.fock_b.sum()),
-           "T": [float(x.sum()) for x in T]}
+    """Sums of absolute values (no cancellation: the same-spin doubles are
+    antisymmetric and sum to zero)."""
+    a = lambda x: float(np.abs(x).sum())  # noqa: E731
+    out = {"B": a(s.B), "fock_a": a(s.fock_a), "fock_b": a(s.fock_b), "T": [a(x) for x in T]}
     if d is not None:
-        out["d"] = [float(np.abs(x).sum()) for x in d]
+        out["d"] = [a(x) for x in d]
     return out
 
 
