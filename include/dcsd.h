@@ -27,7 +27,10 @@
  *     T2aa, T2bb [o][o][v][v]   antisymmetric in (i,j) and in (a,b)
  *     T2ab      [o][o][v][v]    (alpha occ i, beta occ j, alpha vir a, beta vir b).
  * The excitation Phi_ref -> the other determinant is T2ab[o-1][o-1][0][0]
- * in both frames; its amplitude must be zero (Section II, text after Eq. 4).
+ * in both frames; for the 2D methods its amplitude must be zero (Section
+ * II, text after Eq. 4); for the fixed-reference methods the library uses
+ * the fixed value (+1 or -1) there, whatever the array holds, and returns
+ * that value in solved amplitudes.
  * Fock matrices passed to dcsd_init are those of Phi_A; for ref = 1 the
  * library uses the alpha matrix as beta and vice versa (spin flip).
  *
@@ -58,7 +61,23 @@ typedef enum {
     DCSD_ERR_NO_DEVICE = 7     /* no CUDA device of compute capability 10.3 */
 } dcsd_status;
 
-typedef enum { DCSD_CCSD = 0, DCSD_DCSD = 1 } dcsd_method;
+/* Methods.  0, 1: the two-determinant 2D-CCSD / 2D-DCSD of Section II
+ * (Eqs. 2-4).  2..5: the fixed-reference FR-CCSD / FR-DCSD of the paper's
+ * introduction (Section I): the doubles amplitude of the excitation
+ * Phi_ref -> other determinant is held at a fixed value, +1 for the
+ * open-shell singlet (_S) or -1 for the M_s = 0 triplet (_T) in this
+ * library's phase of Phi_B (Phi_B = E_{A->B} Phi_A, singlet Phi_A + Phi_B),
+ * all other amplitudes obey the single-reference CCSD / DCSD equations on
+ * Phi_ref, and there are no M W terms.  The FR energy is the single-reference
+ * Delta E = <ref|H_N exp(T)|ref>, which includes the fixed amplitude. */
+typedef enum {
+    DCSD_CCSD = 0,
+    DCSD_DCSD = 1,
+    DCSD_FR_CCSD_S = 2,
+    DCSD_FR_DCSD_S = 3,
+    DCSD_FR_CCSD_T = 4,
+    DCSD_FR_DCSD_T = 5
+} dcsd_method;
 typedef enum { DCSD_MEM_HOST = 0, DCSD_MEM_DEVICE = 1 } dcsd_mem_kind;
 
 /* Arithmetic of the dense contractions (ladder, ring, DF builds).  The
@@ -107,8 +126,10 @@ typedef struct {
 typedef struct {
     double dEA;       /* Delta E_A = <A|H_N exp(T_A)|A>  (Eq. 2)            */
     double W;         /* <B|H_N exp(T_A)|A>, coupling of the two references */
-    double E_S;       /* singlet correlation energy dE_A + W                */
-    double E_T;       /* triplet correlation energy dE_A - W                */
+    double E_S;       /* singlet correlation energy dE_A + W (FR methods:
+                         dE_A for the _S methods, NaN for the _T ones)     */
+    double E_T;       /* triplet correlation energy dE_A - W (FR methods:
+                         dE_A for the _T methods, NaN for the _S ones)     */
     double max_r;     /* max |R| of the last residual                       */
     int iters;        /* residual evaluations performed                     */
     int converged;    /* 1 if max_r <= tol                                   */
@@ -129,16 +150,44 @@ typedef struct {
  *            copies them.
  *   stream : cudaStream_t every call of this context enqueues on (NULL =
  *            legacy default stream).
- * Allocates all device memory the context needs for FP64 and BF16 paths.
+ * Allocates the device memory of the FP64 residual and energy (device
+ * pointers).  Everything else a call may need -- the tensor-core operand
+ * buffers and FP32 accumulator of the BF16* precisions, the DIIS history
+ * of dcsd_solve, the defect vector of the MIXED solve, the staging buffers
+ * of host-memory (mem_kind HOST) calls -- is allocated by dcsd_reserve
+ * ahead of time, or else by the first call that needs it (grow-only, kept
+ * until dcsd_destroy).  dcsd_vjp and dcsd_lambda allocate their recorded
+ * intermediates for the duration of the call.
  * Errors: INVALID_ARG (sizes < bounds, NULL pointers), OOM, CUDA, NO_DEVICE. */
 dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const double* eps,
                       const double* fock_a, const double* fock_b,
                       const double* B, int mem_kind, void* stream);
 
+/* dcsd_reserve -- allocate now every device buffer that later calls of
+ * this context would otherwise allocate on first use: dcsd_residual and
+ * dcsd_energy at `precision` (DCSD_PREC_MIXED: the BF16 and BF16X6
+ * residuals and the defect vector of the MIXED solve), dcsd_solve with up
+ * to diis_n DIIS vectors (0: the two vectors of a Jacobi-only solve), and,
+ * if host_staging is 1, the device staging of mem_kind HOST calls.  After
+ * it, those calls allocate nothing (so that no allocation happens in the
+ * middle of a solve, and memory use is known up front); device memory is
+ * not released before dcsd_destroy.  The tensor-core buffers are sized by
+ * running one CCSD residual at zero amplitudes in each of those precisions
+ * (their sizes depend only on the dimensions); the context's amplitude
+ * buffers are overwritten.  Synchronises the context stream.  Not part of
+ * the paper's method: memory management of this library.
+ * Errors: INVALID_ARG (bad precision, diis_n outside 0..16, host_staging
+ * not 0/1), OOM, CUDA, TIMEOUT. */
+dcsd_status dcsd_reserve(dcsd_ctx* ctx, int precision, int diis_n, int host_staging);
+
 /* dcsd_residual -- one evaluation of the 2D residual (Eqs. 3-4).
  *   R = R^X(T) + M W with R^X the CCSD (method 0) or DCSD (method 1)
  *   single-reference residual; W = R^X at the A->B double; that element of
  *   R2ab is returned as zero.  dEA receives Delta E_A (Eq. 2).
+ *   Fixed-reference methods (2..5): R = R^X(T) with the A->B amplitude at
+ *   its fixed value and no M W terms; W receives R^X at the fixed
+ *   excitation (not an equation of the method), whose R2ab element is
+ *   returned as zero; dEA receives the FR energy.
  *   T* inputs and R* outputs use the layouts above; mem_kind says whether
  *   they are host (copied in and out inside the call, which then
  *   synchronises the stream) or device pointers (asynchronous on the
@@ -221,7 +270,7 @@ dcsd_status dcsd_profile(dcsd_ctx* ctx, int enable, int reset, double* ms,
  *     <R_bar, R(T)> + dEA_bar * dE_A(T) + W_bar * W(T)
  * with respect to the stored amplitude arrays (every element, as stored;
  * T2aa and T2bb are read as full arrays), the DF factors B and the two Fock
- * matrices of dcsd_init.  The paper has no counterpart; this is the
+ * matrices of dcsd_init (2D methods 0 and 1 only).  The paper has no counterpart; this is the
  * derivative of the Section II residual used for the Lambda equations and
  * the response density of dcsd_lambda.
  *   T1a .. T2ab       : amplitudes, layout of this header.
@@ -266,7 +315,7 @@ dcsd_status dcsd_vjp(dcsd_ctx* ctx, int ref, int method, int precision, int mem_
  * stationarity, dE/df along any perturbation of f equals <gamma, df> once
  * T and Lambda are converged.  The paper has no counterpart; this is the
  * first-order property machinery of the Section II energies.
- *   o          : method, ref, maxiter, diis_n, tol (on max |dL/dT| over the
+ *   o          : method (0 or 1), ref, maxiter, diis_n, tol (on max |dL/dT| over the
  *                independent amplitudes), use_guess (Lambda in L* is the
  *                guess); precision must be DCSD_PREC_FP64.
  *   T1a..T2ab  : converged amplitudes (dcsd_solve), layout of this header.
@@ -332,8 +381,8 @@ dcsd_status dcsd_einsum_host(const char* spec, double alpha, const double* A, in
                              const long* size_b, const long* stride_b, double beta, double* C, int rank_c,
                              const long* size_c, const long* stride_c);
 
-/* dcsd_energy_noalloc -- Delta E_A (the first term of Eq. 2, as returned by
- * dcsd_energy) for callers that cannot allocate device memory: code that is
+/* dcsd_energy_noalloc -- Delta E_A, the value dcsd_energy returns as dEA,
+ * for callers that cannot allocate device memory: code that is
  * capturing a CUDA graph, that hands all device memory to its own pool
  * allocator, or that must keep a fixed footprint.  The paper has no
  * counterpart; this is a service of the library.

@@ -329,6 +329,14 @@ class ElementOracle:
             r += self.dc(i, j, a, b)
         return float(r)
 
+    def ladder(self, i, j, a, b):
+        """The particle-particle ladder piece 1/2 sum_ef tau_ijef <ab||ef> of
+        R2_ijab (the <ab||ef> part of the W_abef term above), one element.
+        Used to show how much of an element a broken ladder would change."""
+        Ba, Bb = self.Bvv(a), self.Bvv(b)
+        g = Ba.T @ Bb - Bb.T @ Ba  # <ab||ef> = (ae|bf) - (af|be)
+        return 0.5 * float(np.sum(self.tau(i, j, slice(None), slice(None)) * g))
+
     def dc(self, i, j, a, b):
         """DCSD - CCSD doubles (``ccsd.dc_delta``) at one element."""
         df = self.df

@@ -46,8 +46,13 @@ def _unvec(x, shapes):
     return tuple(out)
 
 
-def solve(sys, method, ref=0, tol=1e-10, maxiter=200, diis_n=8, T0=None, verbose=False):
-    """Converge the 2D amplitude equations.  Returns (T, info)."""
+def solve(sys, method, ref=0, tol=1e-10, maxiter=200, diis_n=8, T0=None, verbose=False, fixed=None):
+    """Converge the 2D amplitude equations.  Returns (T, info).  With fixed =
+    +1 or -1, the fixed-reference equations of ``fr`` instead (the A->B
+    doubles amplitude held at that value, no M*W terms); info then has E,
+    the single-reference energy, and W is the residual element of the fixed
+    excitation."""
+    from . import fr as frmod
     fr, fro = frames(sys, ref)
     o, v = fr.o, fr.v
     D1, D2 = denominators(fr)
@@ -56,12 +61,19 @@ def solve(sys, method, ref=0, tol=1e-10, maxiter=200, diis_n=8, T0=None, verbose
         T = tuple(np.zeros(s) for s in shapes)
     else:
         T = tuple(np.array(x, dtype=float) for x in T0)
+    if fixed is not None:
+        T = frmod.with_fixed(T, fixed)
     hist_t, hist_e = [], []
     info = {}
     for it in range(1, maxiter + 1):
-        t1, t2 = unpack(o, v, T)
-        t1o, t2o = unpack(o, v, flip_abi(T))
-        R1, R2, W, dE, _, _ = residual_so(fr, fro, method, t1, t2, t1o, t2o)
+        if fixed is not None:
+            T = frmod.with_fixed(T, fixed)
+            t1, t2 = unpack(o, v, T)
+            R1, R2, W, dE = frmod.residual_so(fr, method, t1, t2)
+        else:
+            t1, t2 = unpack(o, v, T)
+            t1o, t2o = unpack(o, v, flip_abi(T))
+            R1, R2, W, dE, _, _ = residual_so(fr, fro, method, t1, t2, t1o, t2o)
         Rp = pack(o, v, R1, R2)
         rmax = max(np.abs(x).max() for x in Rp)
         info = dict(iters=it, max_r=rmax, dEA=dE, W=W)
@@ -96,6 +108,9 @@ def solve(sys, method, ref=0, tol=1e-10, maxiter=200, diis_n=8, T0=None, verbose
             c = np.linalg.solve(Bm, rhs)[:m]
             Tn = _unvec(sum(ci * ti for ci, ti in zip(c, hist_t)), shapes)
         T = Tn
+    if fixed is not None:
+        info.update(E=info["dEA"], converged=info["max_r"] <= tol)
+        return T, info
     H, ev, si = heff(info["dEA"], info["W"])
     info.update(E_S=info["dEA"] + info["W"], E_T=info["dEA"] - info["W"], H=H, evals=ev,
                 singlet_index=si, converged=info["max_r"] <= tol)

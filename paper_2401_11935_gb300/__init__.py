@@ -10,10 +10,10 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib as L
-from ._lib import (CCSD, DCSD, MEM_DEVICE, MEM_HOST, PREC_BF16, PREC_BF16X3, PREC_BF16X6,  # noqa: F401
-                   PREC_FP64, PREC_MIXED, DcsdError, dcsd_heff)
+from ._lib import (CCSD, DCSD, FR_CCSD_S, FR_CCSD_T, FR_DCSD_S, FR_DCSD_T, MEM_DEVICE,  # noqa: F401
+                   MEM_HOST, PREC_BF16, PREC_BF16X3, PREC_BF16X6, PREC_FP64, PREC_MIXED, DcsdError, dcsd_heff)
 
-__all__ = ["Engine", "CCSD", "DCSD", "PREC_FP64", "PREC_BF16", "PREC_BF16X3", "PREC_BF16X6", "PREC_MIXED",
+__all__ = ["Engine", "CCSD", "DCSD", "FR_CCSD_S", "FR_DCSD_S", "FR_CCSD_T", "FR_DCSD_T", "PREC_FP64", "PREC_BF16", "PREC_BF16X3", "PREC_BF16X6", "PREC_MIXED",
            "dcsd_heff", "DcsdError"]
 
 
@@ -49,7 +49,9 @@ class Engine:
             self.stream.synchronize()
             self.ctx = L.dcsd_init(n_c, n_v, naux, None, fa.data_ptr(), fb.data_ptr(), Bt.data_ptr(),
                                    MEM_DEVICE, self.stream.cuda_stream)
-        del fa, fb, Bt
+        # the library holds its own copy; these tensors are kept only as the
+        # differentiable handles of residual_autograd (see inputs())
+        self._inputs = (fa, fb, Bt)
 
     @classmethod
     def from_system(cls, s, **kw):
@@ -69,6 +71,11 @@ class Engine:
         return tuple(t.as_tensor(np.ascontiguousarray(x), dtype=t.float64).cuda() for x in T)
 
     # -- C ABI calls -----------------------------------------------------
+    def reserve(self, precision=PREC_FP64, diis_n=8, host_staging=False):
+        """Allocate up front the device memory of residuals at `precision`,
+        a solve with diis_n DIIS vectors and (optionally) host-memory calls."""
+        L.dcsd_reserve(self.ctx, precision, diis_n, 1 if host_staging else 0)
+
     def residual(self, T, ref=0, method=DCSD, precision=PREC_FP64, out=None):
         """Device call: T are CUDA tensors; returns (R tuple, W, dE_A)."""
         R = out if out is not None else tuple(self.torch.empty_like(x) for x in T)
@@ -136,11 +143,26 @@ class Engine:
                             _ptr(ga) if ga is not None else None, _ptr(gb) if gb is not None else None)
         return Lam, ga, gb, res
 
-    def residual_autograd(self, T, ref=0, method=DCSD):
-        """FP64 residual as a differentiable torch function of the amplitudes:
-        returns (R1a, R1b, R2aa, R2bb, R2ab, W, dE_A) as tensors whose
-        backward pass calls dcsd_vjp."""
-        return _residual_function().apply(self, ref, method, *T)
+    def inputs(self, requires_grad=True):
+        """(fock_a, fock_b, B): device tensors holding the values this engine
+        was created with, as leaves for residual_autograd (their gradients
+        are the Fock-matrix and DF-factor parts of dcsd_vjp).  Modifying them
+        does not change the engine: the library keeps its own copy."""
+        for x in self._inputs:
+            x.requires_grad_(requires_grad)
+        return self._inputs
+
+    def residual_autograd(self, T, ref=0, method=DCSD, inputs=None):
+        """FP64 residual as a differentiable torch function: returns (R1a,
+        R1b, R2aa, R2bb, R2ab, W, dE_A) as tensors whose backward pass calls
+        dcsd_vjp.  Differentiable with respect to the five amplitude tensors
+        T and, when inputs = self.inputs() is passed, to the Fock matrices and
+        the DF factors as well."""
+        if inputs is None:
+            return _residual_function().apply(self, ref, method, *T)
+        if len(inputs) != 3 or any(x is not y for x, y in zip(inputs, self._inputs)):
+            raise ValueError("inputs must be the tensors returned by this engine's inputs()")
+        return _residual_function().apply(self, ref, method, *T, *inputs)
 
     def launches(self):
         return L.dcsd_kernel_launches(self.ctx)
@@ -170,10 +192,13 @@ def _residual_function():
 
     class ResidualFunction(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, engine, ref, method, *T):
-            T = tuple(x.detach().contiguous() for x in T)
+        def forward(ctx, engine, ref, method, *args):
+            # args: the five amplitude tensors, then optionally (fock_a,
+            # fock_b, B), whose values the engine already holds
+            T = tuple(x.detach().contiguous() for x in args[:5])
             R, W, dE = engine.residual(T, ref=ref, method=method, precision=PREC_FP64)
             ctx.engine, ctx.ref, ctx.method = engine, ref, method
+            ctx.n_inputs = len(args) - 5
             ctx.save_for_backward(*T)
             dev = T[0].device
             return (*R, torch.tensor(W, dtype=torch.float64, device=dev),
@@ -185,8 +210,13 @@ def _residual_function():
             Rb = [gi.contiguous() if gi is not None else torch.zeros_like(x) for gi, x in zip(g[:5], T)]
             Wb = float(g[5]) if g[5] is not None else 0.0
             Eb = float(g[6]) if g[6] is not None else 0.0
-            Tb, _, _, _ = ctx.engine.vjp(T, Rbar=Rb, Ebar=Eb, Wbar=Wb, ref=ctx.ref, method=ctx.method)
-            return (None, None, None, *Tb)
+            need = ctx.needs_input_grad[3 + 5:] if ctx.n_inputs else ()
+            want_fock = any(need[:2]) if need else False
+            want_B = bool(need[2]) if need else False
+            Tb, Bb, Fa, Fb = ctx.engine.vjp(T, Rbar=Rb, Ebar=Eb, Wbar=Wb, ref=ctx.ref, method=ctx.method,
+                                            want_B=want_B, want_fock=want_fock)
+            extra = (Fa, Fb, Bb) if ctx.n_inputs else ()
+            return (None, None, None, *Tb, *extra)
 
     _RESIDUAL_FN = ResidualFunction
     return _RESIDUAL_FN

@@ -17,13 +17,14 @@ DCSD_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT",
           6: "NUMERIC", 7: "NO_DEVICE"}
 CCSD, DCSD = 0, 1
+FR_CCSD_S, FR_DCSD_S, FR_CCSD_T, FR_DCSD_T = 2, 3, 4, 5
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
            "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda",
-           "dcsd_coupling_host", "dcsd_einsum_host"]
+           "dcsd_coupling_host", "dcsd_einsum_host", "dcsd_reserve"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -89,6 +90,8 @@ def load():
     view = [P, C.c_int, P, P]
     lib.dcsd_einsum_host.argtypes = [C.c_char_p, C.c_double] + view + view + [C.c_double] + view
     lib.dcsd_einsum_host.restype = C.c_int
+    lib.dcsd_reserve.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.dcsd_reserve.restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -134,6 +137,12 @@ def dcsd_solve(ctx, opts, mem_kind, T, allow_not_converged=True):
     if not (allow_not_converged and st == 4):
         _check(st, ctx)
     return res
+
+
+def dcsd_reserve(ctx, precision, diis_n=8, host_staging=0):
+    """Allocate ahead of time what residuals of `precision`, a solve with
+    diis_n DIIS vectors and (host_staging=1) host-memory calls need."""
+    _check(load().dcsd_reserve(ctx, precision, diis_n, host_staging), ctx)
 
 
 def dcsd_heff(dEA, W):

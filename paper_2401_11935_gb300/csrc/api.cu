@@ -205,7 +205,7 @@ void free_ctx(Ctx* c) {
                        &c->Kref[1][0], &c->Kref[1][1], &c->t1, &c->R1, &c->t2s, &c->Bd, &c->Pbt, &c->fd,
                        &c->fsc, &c->Z, &c->J, &c->H, &c->G, &c->Wo, &c->Foc, &c->Fvi, &c->big0,
                        &c->big1, &c->big2, &c->big3, &c->red, &c->splitk_ws, &c->scal, &c->c1, &c->diis_t,
-                       &c->diis_e, &c->abi[0], &c->abi[1], &c->abi[2], &c->abi[3], &c->abi[4],
+                       &c->diis_e, &c->jac_s, &c->jac_t, &c->defect, &c->abi[0], &c->abi[1], &c->abi[2], &c->abi[3], &c->abi[4],
                        &c->abi[5], &c->abi[6], &c->abi[7], &c->abi[8], &c->abi[9]};
     for (auto pp : ptrs) {
         if (*pp) cudaFree(*pp);
@@ -233,6 +233,26 @@ void free_ctx(Ctx* c) {
 dcsd_status ensure_abi(Ctx* c) {
     if (c->abi[0]) return DCSD_OK;
     for (int k = 0; k < 10; ++k) DCSD_TRY(alloc(c, &c->abi[k], abi_len(c, k % 5)));
+    return DCSD_OK;
+}
+
+// DIIS history of nd vectors of length len (grow-only, kept until destroy)
+dcsd_status ensure_diis(Ctx* c, int nd, long len) {
+    if (nd <= c->diis_cap) return DCSD_OK;
+    if (c->diis_t) cudaFree(c->diis_t);
+    if (c->diis_e) cudaFree(c->diis_e);
+    c->diis_t = c->diis_e = nullptr;
+    c->diis_cap = 0;
+    DCSD_TRY(alloc(c, &c->diis_t, (size_t)nd * len));
+    DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
+    c->diis_cap = nd;
+    return DCSD_OK;
+}
+
+// step / new-amplitude vectors of a Jacobi-only solve (kept until destroy)
+dcsd_status ensure_jacobi(Ctx* c, long len) {
+    if (!c->jac_s) DCSD_TRY(alloc(c, &c->jac_s, len));
+    if (!c->jac_t) DCSD_TRY(alloc(c, &c->jac_t, len));
     return DCSD_OK;
 }
 
@@ -417,7 +437,7 @@ extern "C" dcsd_status dcsd_profile(dcsd_ctx* h, int enable, int reset, double* 
 
 static dcsd_status residual_common(Ctx* c, int ref, int method, int prec, int mem_kind,
                                    const double* const* T, double* const* R, double* W, double* dEA) {
-    if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) || !valid_prec(prec) ||
+    if ((ref != 0 && ref != 1) || !method_valid(method) || !valid_prec(prec) ||
         (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
         c->err = "invalid ref/method/precision/mem_kind";
         return DCSD_ERR_INVALID_ARG;
@@ -495,6 +515,42 @@ extern "C" dcsd_status dcsd_energy(dcsd_ctx* h, int ref, int method, int mem_kin
     return residual_common(&h->c, ref, method, DCSD_PREC_FP64, mem_kind, T, nullptr, W, dEA);
 }
 
+// Reservation: every buffer a residual of the given precision (and a solve
+// with diis_n history vectors, and host-memory staging) touches is allocated
+// now.  The buffers of the tensor-core engine are sized by the contractions
+// that use them and only ever grow, and their sizes depend on the dimensions
+// alone, so one residual at zero amplitudes through the same code path sizes
+// every one of them (CCSD's term set contains every contraction of DCSD).
+extern "C" dcsd_status dcsd_reserve(dcsd_ctx* h, int precision, int diis_n, int host_staging) {
+    if (!h) return DCSD_ERR_INVALID_ARG;
+    Ctx* c = &h->c;
+    if ((!valid_prec(precision) && precision != DCSD_PREC_MIXED) || diis_n < 0 || diis_n > 16 ||
+        (host_staging != 0 && host_staging != 1)) {
+        c->err = "dcsd_reserve: invalid precision, diis_n or host_staging";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    const long len = 2l * c->O * c->V + 3l * c->O * c->O * c->V * c->V;
+    if (host_staging) DCSD_TRY(ensure_abi(c));
+    if (diis_n > 0) DCSD_TRY(ensure_diis(c, diis_n, len));
+    else DCSD_TRY(ensure_jacobi(c, len));
+    int runs[2] = {-1, -1};
+    if (precision == DCSD_PREC_MIXED) {
+        runs[0] = DCSD_PREC_BF16;
+        runs[1] = DCSD_PREC_BF16X6;
+        if (!c->defect) DCSD_TRY(alloc(c, &c->defect, len));
+    } else if (precision != DCSD_PREC_FP64) {
+        runs[0] = precision;
+    }
+    for (int r : runs) {
+        if (r < 0) continue;
+        DCSD_CUDA(c, cudaMemsetAsync(c->t1, 0, len * sizeof(double), c->stream));
+        DCSD_TRY(residual_union(c, 0, DCSD_CCSD, r));
+    }
+    DCSD_TRY(sync_scalars(c, 23));
+    if (tc_timeout(c)) return DCSD_ERR_TIMEOUT;
+    return DCSD_OK;
+}
+
 namespace dcsd {
 dcsd_status vjp_run(Ctx* c, int ref, int method, int prec, const double* const* Td, const double* const* Rb,
                     double Ebar, double Wbar, double* const* Tb, double* Bb, double* Fab, double* Fbb);
@@ -511,6 +567,8 @@ extern "C" dcsd_status dcsd_vjp(dcsd_ctx* h, int ref, int method, int precision,
     const double* T[5] = {T1a, T1b, T2aa, T2bb, T2ab};
     const double* Rb[5] = {R1a_bar, R1b_bar, R2aa_bar, R2bb_bar, R2ab_bar};
     double* Tb[5] = {T1a_bar, T1b_bar, T2aa_bar, T2bb_bar, T2ab_bar};
+    // reverse mode: the 2D methods (the fixed-reference residual has a fixed
+    // amplitude, whose derivative the recorded tape does not exclude)
     if ((ref != 0 && ref != 1) || (method != DCSD_CCSD && method != DCSD_DCSD) || !valid_prec(precision) ||
         (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
         c->err = "invalid ref/method/precision/mem_kind";
@@ -715,15 +773,7 @@ extern "C" dcsd_status dcsd_lambda(dcsd_ctx* h, const dcsd_solve_opts* o, int st
     const long eAB = n1 + (((2l * c->O + frm.occ_act[0]) * c->O + frm.occ_act[1]) * c->V + frm.vir_act[0]) * c->V +
                      frm.vir_act[1];
     const int nd = o->diis_n;
-    if (nd > 0 && c->diis_cap < nd) {
-        if (c->diis_t) cudaFree(c->diis_t);
-        if (c->diis_e) cudaFree(c->diis_e);
-        c->diis_t = c->diis_e = nullptr;
-        c->diis_cap = 0;
-        DCSD_TRY(alloc(c, &c->diis_t, (size_t)nd * len));
-        DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
-        c->diis_cap = nd;
-    }
+    if (nd > 0) DCSD_TRY(ensure_diis(c, nd, len));
     double* sbuf = nd == 0 ? dev(len) : nullptr;
     double* tbuf = nd == 0 ? dev(len) : nullptr;
     if (nd == 0 && (!sbuf || !tbuf)) return DCSD_ERR_OOM;
@@ -849,7 +899,7 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
                                   double* T1b, double* T2aa, double* T2bb, double* T2ab, dcsd_result* res) {
     if (!h || !o || !res) return DCSD_ERR_INVALID_ARG;
     Ctx* c = &h->c;
-    if ((o->ref != 0 && o->ref != 1) || (o->method != DCSD_CCSD && o->method != DCSD_DCSD) ||
+    if ((o->ref != 0 && o->ref != 1) || !method_valid(o->method) ||
         (!valid_prec(o->precision) && o->precision != DCSD_PREC_MIXED) || o->maxiter < 1 ||
         o->diis_n < 0 || o->diis_n > 16 || !(o->tol > 0.0) ||
         (mem_kind != DCSD_MEM_HOST && mem_kind != DCSD_MEM_DEVICE)) {
@@ -882,15 +932,8 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         DCSD_CUDA(c, cudaMemsetAsync(c->t1, 0, len * sizeof(double), c->stream));
     }
     const int nd = o->diis_n;
-    if (nd > 0 && c->diis_cap < nd) {
-        if (c->diis_t) cudaFree(c->diis_t);
-        if (c->diis_e) cudaFree(c->diis_e);
-        c->diis_t = c->diis_e = nullptr;
-        c->diis_cap = 0;
-        DCSD_TRY(alloc(c, &c->diis_t, (size_t)nd * len));
-        DCSD_TRY(alloc(c, &c->diis_e, (size_t)nd * len));
-        c->diis_cap = nd;
-    }
+    if (nd > 0) DCSD_TRY(ensure_diis(c, nd, len));
+    else DCSD_TRY(ensure_jacobi(c, len));
     std::vector<double> Bm(16 * 16, 0.0);
     int nhist = 0, next = 0;
     // MIXED phases: 0 BF16, 1 BF16X6, 2 FP64
@@ -901,11 +944,8 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     int stall = 0;
     const double* fa = c->fock[ref == 0 ? 0 : 1];
     const double* fb = c->fock[ref == 0 ? 1 : 0];
-    double *sbuf = nullptr, *tbuf = nullptr;
-    if (nd == 0) {
-        DCSD_TRY(alloc(c, &sbuf, len));
-        DCSD_TRY(alloc(c, &tbuf, len));
-    }
+    double* sbuf = c->jac_s;
+    double* tbuf = c->jac_t;
     dcsd_status status = DCSD_ERR_NOT_CONVERGED;
     res->converged = 0;
     res->switched_at = -1;
@@ -916,11 +956,6 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
     // R64 at the outer T and differs from R64 nearby only by the change of
     // the tensor cores' rounding error.  Convergence is declared on outer
     // (FP64) residuals only.
-    double* defect = nullptr;
-    struct FreeDefect {
-        double*& p;
-        ~FreeDefect() { if (p) cudaFree(p); }
-    } free_defect{defect};
     bool outer = true;
     int inner = 0;
     double inner_best = 1e300;
@@ -935,7 +970,7 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         dcsd_status s = residual_union(c, ref, o->method, prec);
         if (s != DCSD_OK) { status = s; break; }
         if (refining && !outer) {
-            if ((s = axpy_view(c, -1.0, view(defect, {len}), 1.0, Rall)) != DCSD_OK) { status = s; break; }
+            if ((s = axpy_view(c, -1.0, view(c->defect, {len}), 1.0, Rall)) != DCSD_OK) { status = s; break; }
         }
         if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
         DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
@@ -960,7 +995,8 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         }
         if (refining && outer) {
             // e = R_X6(T) - R64(T); the step below uses R64
-            if (!defect && (s = alloc(c, &defect, len)) != DCSD_OK) { status = s; break; }
+            if (!c->defect && (s = alloc(c, &c->defect, len)) != DCSD_OK) { status = s; break; }
+            double* defect = c->defect;
             DCSD_CUDA(c, cudaMemcpyAsync(defect, c->R1, len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
             if ((s = residual_union(c, ref, o->method, DCSD_PREC_BF16X6)) != DCSD_OK) { status = s; break; }
             if ((s = axpy_view(c, 1.0, Rall, -1.0, view(defect, {len}))) != DCSD_OK) { status = s; break; }
@@ -1074,11 +1110,15 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         trace_end(c);
         if ((s = launch_check(c, "diis_extrapolate")) != DCSD_OK) { status = s; break; }
     }
-    if (sbuf) cudaFree(sbuf);
-    if (tbuf) cudaFree(tbuf);
     res->iters = std::min(it, o->maxiter);
     res->E_S = res->dEA + res->W;
     res->E_T = res->dEA - res->W;
+    if (method_fr(o->method)) {
+        // one state: its energy is the single-reference Delta E
+        const bool singlet = method_fr_value(o->method) > 0.0;
+        res->E_S = singlet ? res->dEA : std::nan("");
+        res->E_T = singlet ? std::nan("") : res->dEA;
+    }
     res->switched_at = switched_at;
     res->polished_at = polished_at;
     // amplitudes out

@@ -190,6 +190,9 @@ struct Ctx {
     double* diis_t = nullptr;     // [nd][len]
     double* diis_e = nullptr;     // [nd][len]
     int diis_cap = 0;
+    double* jac_s = nullptr;      // [len] Jacobi step and new amplitudes when no DIIS history is kept
+    double* jac_t = nullptr;
+    double* defect = nullptr;     // [len] MIXED solve: defect e = R_X6(T) - R64(T) of the last outer step
 };
 
 // ---------------------------------------------------------------------------
@@ -279,6 +282,15 @@ void mtables_free(Ctx* c);
 dcsd_status merge_r2f(Ctx* c);
 // coupling terms; fp32 = evaluate the doubles coefficient products in FP32
 dcsd_status apply_mterms(Ctx* c, int ref, bool fp32);
+// fixed-reference methods: zero the non-amplitude positions and the fixed
+// A->B element of the residual; set the fixed amplitude in c->t2
+dcsd_status apply_fr_mask(Ctx* c, int ref);
+dcsd_status set_fixed_amplitude(Ctx* c, int ref, double value);
+// method codes (dcsd_method): DC modification, fixed-reference flag, fixed value
+inline bool method_valid(int m) { return m >= DCSD_CCSD && m <= DCSD_FR_DCSD_T; }
+inline bool method_dc(int m) { return m == DCSD_DCSD || m == DCSD_FR_DCSD_S || m == DCSD_FR_DCSD_T; }
+inline bool method_fr(int m) { return m >= DCSD_FR_CCSD_S; }
+inline double method_fr_value(int m) { return m >= DCSD_FR_CCSD_T ? -1.0 : 1.0; }
 
 // residual orchestration (residual.cu)
 dcsd_status residual_union(Ctx* c, int ref, int method, int precision);

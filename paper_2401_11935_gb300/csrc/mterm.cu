@@ -1027,6 +1027,56 @@ dcsd_status apply_mterms(Ctx* c, int ref, bool fp32) {
     return launch_check(c, "mterm_doubles");
 }
 
+// Fixed-reference methods (no coupling terms): the residual positions that
+// are not amplitudes of the frame (padding of the union layout, same-spin
+// diagonals) and the fixed A->B element are set to zero, the same masking
+// that the coupling kernels apply to the 2D residual.
+__global__ void k_fr_mask(MArgs a) {
+    const long O = a.O, V = a.V, n1 = 2 * O * V, total = n1 + 3 * O * O * V * V;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        bool ok;
+        if (e < n1) {
+            const int s = (int)(e / (O * V)), i = (int)((e / V) % O), x = (int)(e % V);
+            ok = occ_ok(a, s, i) && vir_ok(a, s, x);
+            if (!ok) a.R1[e] = 0.0;
+            continue;
+        }
+        const long r = e - n1;
+        const int blk = (int)(r / (O * O * V * V));
+        const int i = (int)((r / (O * V * V)) % O), j = (int)((r / (V * V)) % O);
+        const int x = (int)((r / V) % V), b = (int)(r % V);
+        const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+        ok = occ_ok(a, s1, i) && occ_ok(a, s2, j) && vir_ok(a, s1, x) && vir_ok(a, s2, b);
+        if (blk != 2 && (i == j || x == b)) ok = false;
+        if (blk == 2 && i == a.occ_act[s1] && j == a.occ_act[s2] && x == a.vir_act[s1] && b == a.vir_act[s2])
+            ok = false;
+        if (!ok) a.R2[r] = 0.0;
+    }
+}
+
+__global__ void k_set_value(double* p, double v) { *p = v; }
+
+dcsd_status apply_fr_mask(Ctx* c, int ref) {
+    MArgs a;
+    a.O = c->O; a.V = c->V; a.nc = c->nc; a.ref = ref;
+    Frame f = frame_of(c, ref);
+    for (int s = 0; s < 2; ++s) { a.occ_act[s] = f.occ_act[s]; a.vir_act[s] = f.vir_act[s]; }
+    a.t1 = c->t1; a.t2 = c->t2; a.t2s = c->t2s; a.R1 = c->R1; a.R2 = c->R2; a.c1 = c->c1;
+    a.W = c->scal;
+    const long total = 2l * c->O * c->V + 3l * c->O * c->O * c->V * c->V;
+    const long blocks = std::min<long>((total + 255) / 256, (long)std::max(c->num_sms, 1) * 8);
+    k_fr_mask<<<(unsigned)std::max<long>(1, blocks), 256, 0, c->stream>>>(a);
+    return launch_check(c, "fr_mask");
+}
+
+dcsd_status set_fixed_amplitude(Ctx* c, int ref, double value) {
+    const Frame f = frame_of(c, ref);
+    const long O = c->O, V = c->V;
+    const long e = (((2 * O + f.occ_act[0]) * O + f.occ_act[1]) * V + f.vir_act[0]) * V + f.vir_act[1];
+    k_set_value<<<1, 1, 0, c->stream>>>(c->t2 + e, value);
+    return launch_check(c, "set_fixed_amplitude");
+}
+
 }  // namespace dcsd
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,11 @@
 // DC (Section II: DC applied to the doubles as in single-reference DCSD): the
 // exchange part of the quadratic ring is dropped (x = 0) and the two
 // Fock-like quadratic terms are halved (y = 1/2); CCSD has x = y = 1.
+//
+// Fixed-reference (FR) methods (the approach of the paper's introduction):
+// the A->B doubles amplitude is held at +1 (singlet) or -1 (M_s = 0
+// triplet), the other amplitudes obey the single-reference equations, and
+// the M W coupling terms are absent.
 #include "common.h"
 
 namespace dcsd {
@@ -119,8 +124,8 @@ dcsd_status merge_r2f(Ctx* c) {
 
 dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
-    const double x = method == DCSD_CCSD ? 1.0 : 0.0;
-    const double y = method == DCSD_CCSD ? 1.0 : 0.5;
+    const double x = method_dc(method) ? 0.0 : 1.0;
+    const double y = method_dc(method) ? 0.5 : 1.0;
     const Frame fr = frame_of(c, ref);
     const int nsplit = prec == DCSD_PREC_BF16X6 ? 3 : prec == DCSD_PREC_BF16X3 ? 2 : 1;
     auto big = [&](const char* spec, double alpha, const TV& A, const TV& Bm, double beta,
@@ -157,6 +162,9 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         }
         return einsum64(c, spec, alpha, A, Bm, beta, C);
     };
+
+    // fixed-reference methods: the A->B amplitude takes its fixed value
+    if (method_fr(method)) DCSD_TRY(set_fixed_amplitude(c, ref, method_fr_value(method)));
 
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
@@ -419,7 +427,10 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
         DCSD_TRY(copy_dev(c, c->scal, c->R2 + e, 1));
     }
-    DCSD_TRY(apply_mterms(c, ref, fast));
+    // fixed-reference methods have no coupling terms (the element just read
+    // is then the single-reference residual of the fixed excitation)
+    if (method_fr(method)) DCSD_TRY(apply_fr_mask(c, ref));
+    else DCSD_TRY(apply_mterms(c, ref, fast));
     return DCSD_OK;
 }
 

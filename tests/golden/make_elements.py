@@ -7,13 +7,20 @@ run uses (``python -m paper_2401_11935_gb300 residual --dims <name>``:
 synth.random_amplitudes with seed 3, magnitude 1e-3, reference A), the
 method 2D-DCSD.  Stored: Delta E_A (first term of Eq. 2), W (the A->B
 residual element) and sampled elements of R1a, R1b, R2aa, R2bb, R2ab
-(Eqs. 3-4), at fixed pseudo-random positions; and, for the reverse mode, the
-derivative of one R2ab element along a seeded direction d (fourth-order
-central stencil of the element-wise oracle).  Checksums of the generated
-inputs let a consumer detect inputs that differ from these (another numpy
-random stream).
+(Eqs. 3-4); for each doubles element also its particle-particle ladder
+piece 1/2 sum_ef tau_ijef <ab||ef>, so that a consumer can check that its
+tolerance is far below what a missing or misplaced ladder contribution
+would change.  The doubles positions are stratified: per block, random
+positions plus positions whose first virtual index lies in the first or in
+the last rows of the virtual range (the first and last integral chunks of a
+ladder that is built row block by row block), with the second virtual index
+on either side of the first, and, for the same-spin blocks, rows with i > j
+as well as i < j.  For the reverse mode: the derivative of one R2ab element
+along a seeded direction d (fourth-order central stencil of the
+element-wise oracle).  Checksums of the generated inputs let a consumer
+detect inputs that differ from these (another numpy random stream).
 
-Usage: python tests/golden/make_elements.py c5 [n_samples]
+Usage: python tests/golden/make_elements.py c5 [n_random_per_block]
 """
 import json
 import os
@@ -52,36 +59,58 @@ def checksums(s, T, d=None):
     return out
 
 
-def positions(s, n, rng):
-    """n element positions per block: same-spin diagonals excluded, and only
-    excitations whose orbital Z2 labels add up to even (the others vanish by
-    the symmetry of the synthetic Hamiltonian)."""
-    o, v = s.n_c + 1, s.n_v + 1
+def _allowed(s, blk, idx):
+    """Excitations whose orbital Z2 labels add up to even (the others vanish
+    by the symmetry of the synthetic Hamiltonian); same-spin diagonals
+    excluded."""
     oa, ob, va, vb = frame_orbitals(s.n_c, s.n_v, REF)
     par = s.parity
-    occ = (oa, ob, oa)   # spins of i (and j) per block: R1a, R1b / R2aa, R2bb, R2ab
-    vir = (va, vb, va)
-    occ2 = (oa, ob, ob)
-    vir2 = (va, vb, vb)
+    if blk < 2:
+        occ, vir = (oa, ob)[blk], (va, vb)[blk]
+        i, a = idx
+        return not (par[occ[i]] ^ par[vir[a]])
+    b3 = blk - 2
+    i, j, a, b = idx
+    if b3 < 2 and (i == j or a == b):
+        return False
+    o1, o2 = ((oa, oa), (ob, ob), (oa, ob))[b3]
+    v1, v2 = ((va, va), (vb, vb), (va, vb))[b3]
+    return not (par[o1[i]] ^ par[o2[j]] ^ par[v1[a]] ^ par[v2[b]])
+
+
+def positions(s, n_random, rng, edge=7):
+    """Per block: n_random random positions (singles: 2 n_random); for the
+    doubles also 8 targeted ones: a in the first or last `edge` virtual
+    rows, b < a or b > a, and (same-spin blocks) i < j or i > j."""
+    o, v = s.n_c + 1, s.n_v + 1
     out = []
+
+    def draw(blk, make):
+        while True:
+            idx = make()
+            if _allowed(s, blk, idx):
+                return idx
     for blk in range(5):
-        k = 0
-        while k < n:
-            if blk < 2:
-                i, a = int(rng.integers(o)), int(rng.integers(v))
-                if par[occ[blk][i]] ^ par[vir[blk][a]]:
-                    continue
-                idx = (i, a)
-            else:
-                b3 = blk - 2
-                i, j, a, b = (int(x) for x in (rng.integers(o), rng.integers(o), rng.integers(v), rng.integers(v)))
-                if b3 < 2 and (i == j or a == b):
-                    continue
-                if par[occ[b3][i]] ^ par[occ2[b3][j]] ^ par[vir[b3][a]] ^ par[vir2[b3][b]]:
-                    continue
-                idx = (i, j, a, b)
-            out.append((blk, idx))
-            k += 1
+        if blk < 2:
+            for _ in range(2 * n_random):
+                idx = draw(blk, lambda: (int(rng.integers(o)), int(rng.integers(v))))
+                out.append((blk, idx, "random"))
+            continue
+        for _ in range(n_random):
+            idx = draw(blk, lambda: tuple(int(x) for x in (rng.integers(o), rng.integers(o),
+                                                            rng.integers(v), rng.integers(v))))
+            out.append((blk, idx, "random"))
+        for region in ("first", "last"):
+            for side in ("b<a", "b>a"):
+                for rows in ("i<j", "i>j"):
+                    def make():
+                        a = int(rng.integers(1, edge)) if region == "first" else int(rng.integers(v - edge, v - 1))
+                        b = int(rng.integers(0, a)) if side == "b<a" else int(rng.integers(a + 1, v))
+                        i, j = sorted(int(x) for x in rng.choice(o, 2, replace=False))
+                        if rows == "i>j":
+                            i, j = j, i
+                        return (i, j, a, b)
+                    out.append((blk, draw(blk, make), f"{region} {side} {rows}"))
     return out
 
 
@@ -94,10 +123,13 @@ def main(name, n):
            "ref": REF, "method": "2D-DCSD", "generator": "synth.make_system + synth.random_amplitudes",
            "oracle": "oracle/element.py", "W": eo.W(), "dEA": eo.energy(), "elements": []}
     print(name, "W", res["W"], "dEA", res["dEA"], flush=True)
-    for blk, idx in positions(s, n, np.random.default_rng(11)):
+    for blk, idx, kind in positions(s, n, np.random.default_rng(11)):
         val = element.residual_element(eo, blk, idx)
-        res["elements"].append({"block": blk, "index": list(idx), "value": val})
-        print(blk, idx, val, flush=True)
+        rec = {"block": blk, "index": list(idx), "kind": kind, "value": val}
+        if blk >= 2:
+            rec["ladder"] = eo.ladder(*element.abi_to_so(eo.o, eo.v, blk, idx))
+        res["elements"].append(rec)
+        print(blk, idx, kind, val, rec.get("ladder"), flush=True)
     # reverse mode: d/de R_q(T + e d) for the first sampled R2ab element
     q = next(e for e in res["elements"] if e["block"] == 4)
     d = direction(T)
@@ -115,4 +147,4 @@ def main(name, n):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "c5", int(sys.argv[2]) if len(sys.argv) > 2 else 2)
+    main(sys.argv[1] if len(sys.argv) > 1 else "c5", int(sys.argv[2]) if len(sys.argv) > 2 else 4)

@@ -2,7 +2,10 @@
 
 Calls only the CPU oracle (oracle/) and the seeded generator (synth/).
 Usage: python tests/golden/make_golden.py c1 [c2 ...]
-The GPU tests compare the library's converged energies with these files.
+The GPU tests compare the library's converged energies with these files:
+2D-CCSD and 2D-DCSD (Section II), and the fixed-reference FR-CCSD and
+FR-DCSD (Section I) for the singlet (fixed amplitude +1) and the M_s = 0
+triplet (-1).
 """
 import json
 import os
@@ -31,6 +34,16 @@ def main(names):
             out["results"][mname]["converged"] = bool(info["converged"])
             out["results"][mname]["oracle_seconds"] = time.time() - t0
             print(name, mname, out["results"][mname], flush=True)
+        for method, mname in ((0, "FR-CCSD"), (1, "FR-DCSD")):
+            for sign, st in ((1.0, "S"), (-1.0, "T")):
+                t0 = time.time()
+                _, info = solve.solve(s, method, ref=0, tol=TOL[name], maxiter=300, fixed=sign)
+                key = f"{mname} {st}"
+                out["results"][key] = {k: float(info[k]) for k in ("E", "W", "max_r")}
+                out["results"][key]["iters"] = int(info["iters"])
+                out["results"][key]["converged"] = bool(info["converged"])
+                out["results"][key]["oracle_seconds"] = time.time() - t0
+                print(name, key, out["results"][key], flush=True)
         with open(os.path.join(HERE, f"{name}_energies.json"), "w") as f:
             json.dump(out, f, indent=1)
 

@@ -5,12 +5,14 @@ example while capturing a CUDA graph); its working memory is a fixed array
 inside the library.  This file is collected last so that a failure here
 does not hide the results of the other GPU tests; it passes alone and after
 them.  Two calls in a row (with different amplitudes) must each match the
-context-based dcsd_energy to the energy tolerance of the parity tests.
+context-based dcsd_energy to the energy tolerance of the parity tests, and
+the CPU oracle's Delta E_A as well.
 """
 import numpy as np
 import pytest
 
 from synth import make_system, random_amplitudes
+from oracle import twod
 
 pytestmark = pytest.mark.gpu
 
@@ -34,13 +36,16 @@ def test_energy_noalloc_matches_energy_twice():
         out = torch.zeros(1, dtype=torch.float64, device=dev)
         stream = torch.cuda.current_stream().cuda_stream
         for k, scale in enumerate((0.02, 0.05)):  # two calls in a row
-            T = eng.to_device(random_amplitudes(s, seed=seed + 10 * k, ref=ref, scale1=scale, scale2=scale))
+            Th = random_amplitudes(s, seed=seed + 10 * k, ref=ref, scale1=scale, scale2=scale)
+            T = eng.to_device(Th)
             dEA_ref, _ = eng.energy(T, ref=ref)
+            _, _, dEA_oracle = twod.residual(s, ref, twod.DCSD, Th)
             out.fill_(np.nan)
             L.dcsd_energy_noalloc(s.n_c, s.n_v, s.naux, ref, fa.data_ptr(), fb.data_ptr(), Bt.data_ptr(),
                                   [x.data_ptr() for x in T], out.data_ptr(), stream)
             torch.cuda.synchronize()
             assert abs(float(out.item()) - dEA_ref) < TOL_E, (ref, k, float(out.item()), dEA_ref)
+            assert abs(float(out.item()) - dEA_oracle) < TOL_E, (ref, k, float(out.item()), dEA_oracle)
         eng.close()
 
 
