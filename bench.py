@@ -10,8 +10,12 @@ update.  Contractions run in BF16 on the tcgen05 tensor cores (the first
 phase of the mixed-precision solve); denominators, DIIS, energies and the
 residual norm are FP64.
 
-Prints one JSON line.  --impl reference times the CPU oracle instead (a
-bounded sample, scaled to the same workload).
+Prints one JSON line.  Besides the timed iteration it carries the
+mixed-precision solve against the FP64 solve (second named workload), the
+CPU oracle on a bounded sample of the same workload (cpu_baseline) and the
+oracle and the GPU on the same small configuration
+(cpu_baseline_same_config).  --impl reference times the CPU oracle instead
+(elements of the same workload, scaled to seconds per iteration).
 """
 from __future__ import annotations
 
@@ -35,9 +39,10 @@ UNIT = "s/iteration"
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum averaged over the 72 ladder
-# GEMM launches (36 producer, 34 scatter consumer, 2 G-pass consumer) of one c5
-# BF16 residual, from the one-pass ncu capture summarised in
-# profiles/launches_c5_bf16_iteration.md (K-blocked ladder operands)
+# GEMM launches (36 producer, 34 scatter consumer, 2 G-pass consumer) of one
+# 30+2 / 500 / 1500 BF16 residual, from a one-pass ncu capture of this
+# benchmark with the K-blocked ladder operands; set to None whenever the
+# ladder kernels change until a new capture replaces it
 LADDER_DRAM_BYTES_PER_LAUNCH = 7.476e9
 
 
@@ -117,49 +122,171 @@ def whole_job_value(t_step, world):
     return t_step / world if world > 1 else t_step
 
 
-def oracle_sample(seconds_budget=20.0, workload=WORKLOAD):
-    """Time the CPU oracle (as it stands) on a bounded sample: one 2D-DCSD
-    residual of a reduced system with the same structure, scaled to the
-    workload by the ratio of o^2 v^4 ladder operation counts."""
-    from synth import make_system, random_amplitudes
-    from oracle import twod
-    nc, nv, X = 6, 40, 120
-    s = make_system((nc, nv, X), seed=7)
-    T = random_amplitudes(s, seed=8)
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def element_counts(nc, nv):
+    """Residual elements of one iteration in the amplitude layout: singles
+    2 o v, doubles 3 o^2 v^2 (o = n_c + 1, v = n_v + 1 per spin)."""
+    o, v = nc + 1, nv + 1
+    return 2 * o * v, 3 * o * o * v * v
+
+
+class ElementSampler:
+    """The element-wise CPU oracle (as it stands) on the benchmark workload
+    itself: builds the inputs and the oracle once, then evaluates residual
+    elements one at a time.  One iteration of the workload costs, for this
+    oracle, the evaluation of every residual element, so the seconds per
+    iteration are estimated as n_singles * t_singles + n_doubles * t_doubles
+    from the timed elements."""
+
+    def __init__(self, workload):
+        from synth import make_system, random_amplitudes
+        from oracle import element
+        t0 = time.perf_counter()
+        self.element = element
+        self.s = make_system(workload)
+        T = random_amplitudes(self.s, seed=3, ref=0, scale1=1e-3, scale2=1e-3)
+        self.eo = element.ElementOracle(self.s, 0, 1, T)
+        self.setup_s = time.perf_counter() - t0
+        self.rng = np.random.default_rng(17)
+        self.n1, self.n2 = element_counts(self.s.n_c, self.s.n_v)
+
+    def one(self, doubles):
+        o, v = self.s.o, self.s.v
+        r = self.rng
+        if doubles:
+            blk, idx = int(r.integers(2, 5)), tuple(int(x) for x in (r.integers(o), r.integers(o),
+                                                                       r.integers(v), r.integers(v)))
+        else:
+            blk, idx = int(r.integers(0, 2)), (int(r.integers(o)), int(r.integers(v)))
+        self.eo._cache.clear()  # every element pays for its own intermediates
+        t0 = time.perf_counter()
+        self.element.residual_element(self.eo, blk, idx)
+        return time.perf_counter() - t0
+
+    def w_once(self):
+        """W (the A->B doubles element) enters every element through the
+        coupling terms and is computed once per residual, i.e. once per
+        7e8 elements: its cost is left out of the estimate, and the timed
+        elements use a placeholder value (their values are not used)."""
+        self.eo._W = 0.0
+
+
+def oracle_sample(workload=WORKLOAD):
+    """cpu_baseline: one singles and one doubles element of the workload by
+    the element-wise oracle, scaled to seconds per iteration by the element
+    counts (about a minute of CPU including the input build)."""
+    es = ElementSampler(workload)
+    es.w_once()
+    t1 = es.one(False)
+    t2 = es.one(True)
+    val = es.n1 * t1 + es.n2 * t2
+    return {"value": val, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"element-wise oracle on the {workload} workload: one singles element "
+                      f"({t1:.1f} s) and one doubles element ({t2:.1f} s), scaled by the "
+                      f"{es.n1} singles and {es.n2} doubles elements of one residual "
+                      f"(inputs and oracle built in {es.setup_s:.0f} s, not counted)"}
+
+
+def oracle_solve_c1():
+    """The full CPU oracle as it stands: one converged 2D-DCSD solve of the
+    smallest named workload (4 core + 2 open, 20 virtuals, naux 60)."""
+    from synth import make_system
+    from oracle import solve
+    s = make_system("c1")
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        twod.residual(s, 0, twod.DCSD, T)
-        n += 1
-        if time.perf_counter() - t0 > seconds_budget or n >= 50:
-            break
-    dt = (time.perf_counter() - t0) / n
-    c = __import__("synth").CONFIGS[workload]
-    scale = ((c[0] + 1) ** 2 * (c[1] + 1) ** 4) / ((nc + 1) ** 2 * (nv + 1) ** 4)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": dt * scale, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} oracle 2D-DCSD residual(s) at n_c={nc}, n_v={nv}, naux={X} "
-                      f"({dt:.3f} s each) scaled by the o^2 v^4 ladder operation count "
-                      f"to n_c={c[0]}, n_v={c[1]} (x{scale:.3g})"}
+    _, info = solve.solve(s, 1, ref=0, tol=1e-10, maxiter=100)
+    dt = time.perf_counter() - t0
+    return {"s_per_solve": dt, "iters": int(info["iters"]), "s_per_iteration": dt / info["iters"],
+            "E_S": float(info["E_S"]), "E_T": float(info["E_T"]), "cores": _cores()}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle on the benchmark workload.  Each
+    step is one residual element by the element-wise oracle (singles
+    elements; one doubles element is timed during the untimed set-up), and
+    the value is the estimated seconds per iteration (every element of one
+    residual)."""
     if rank != 0:
         return 0
     from synth import CONFIGS
     nc, nv, X, _, _ = CONFIGS[args.config]
-    cb = oracle_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)), workload=args.config)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+    es = ElementSampler(args.config)
+    es.w_once()
+    t2 = es.one(True)
+    for _ in range(args.warmup):
+        es.one(False)
+    t0 = time.perf_counter()
+    t1s = [es.one(False) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    t1 = float(np.mean(t1s))
+    val = es.n1 * t1 + es.n2 * t2
+    cb = {"value": val, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+          "sample": f"element-wise oracle on the {args.config} workload: {args.steps} timed singles elements "
+                    f"({t1:.2f} s each) and one doubles element ({t2:.1f} s), scaled by the {es.n1} singles "
+                    f"and {es.n2} doubles elements of one residual"}
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": cb["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "ms_per_step": wall / max(1, args.steps) * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.config, "n_c": nc, "n_open": 2, "n_v": nv, "naux": X,
                        "method": "2D-DCSD", "reference": "A", "precision": "FP64 CPU oracle",
-                       "parallelism": "single process (rank 0)"},
+                       "parallelism": "single process (rank 0)",
+                       "step": "one residual element (ms_per_step is the time of one step, not of an iteration)"},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def mixed_vs_fp64(P, workload="c2", tol=1e-8):
+    """The mixed-precision 2D-DCSD solve (BF16, then BF16X6, then defect
+    correction with FP64 outer residuals) against the FP64 GPU solve of the
+    second named workload (10 core + 2 open, 120 virtuals, naux 360): seconds
+    per converged solve and the singlet / triplet energy differences, and
+    both against the oracle's converged energies when the stored file of
+    that workload has them."""
+    from synth import make_system
+    s = make_system(workload)
+    eng = P.Engine.from_system(s)
+    eng.reserve(P.PREC_MIXED, diis_n=8)
+    _, f = eng.solve(method=P.DCSD, precision=P.PREC_FP64, tol=tol, maxiter=80)
+    _, m = eng.solve(method=P.DCSD, precision=P.PREC_MIXED, tol=tol, maxiter=80)
+    eng.close()
+    out = {"workload": workload, "method": "2D-DCSD", "tol": tol,
+           "fp64_s_per_solve": f.seconds, "fp64_iters": f.iters, "mixed_s_per_solve": m.seconds,
+           "mixed_iters": m.iters, "speedup": f.seconds / m.seconds if m.seconds > 0 else None,
+           "converged": bool(f.converged and m.converged),
+           "E_S_mixed_minus_fp64": m.E_S - f.E_S, "E_T_mixed_minus_fp64": m.E_T - f.E_T,
+           "gap_mixed_minus_fp64": (m.E_S - m.E_T) - (f.E_S - f.E_T)}
+    path = os.path.join(ROOT, "tests", "golden", f"{workload}_energies.json")
+    if os.path.exists(path):
+        g = json.load(open(path))["results"].get("2D-DCSD")
+        if g:
+            out.update(E_S_mixed_minus_oracle=m.E_S - g["E_S"], E_T_mixed_minus_oracle=m.E_T - g["E_T"],
+                       E_S_fp64_minus_oracle=f.E_S - g["E_S"], E_T_fp64_minus_oracle=f.E_T - g["E_T"])
+    return out
+
+
+def same_config_c1(P):
+    """The CPU oracle and the GPU on the same configuration, the smallest named
+    workload, where the full oracle finishes a converged solve in seconds:
+    converged 2D-DCSD solves (tol 1e-10), FP64 on both sides."""
+    from synth import make_system
+    o = oracle_solve_c1()
+    s = make_system("c1")
+    eng = P.Engine.from_system(s)
+    eng.reserve(P.PREC_FP64, diis_n=8)
+    eng.solve(method=P.DCSD, precision=P.PREC_FP64, tol=1e-10, maxiter=100)  # warm-up
+    _, g = eng.solve(method=P.DCSD, precision=P.PREC_FP64, tol=1e-10, maxiter=100)
+    eng.close()
+    return {"workload": "c1", "method": "2D-DCSD", "precision": "FP64 both",
+            "oracle": o, "gpu": {"s_per_solve": g.seconds, "iters": g.iters, "s_per_iteration": g.seconds / g.iters,
+                                 "E_S": g.E_S, "E_T": g.E_T},
+            "oracle_over_gpu_per_solve": o["s_per_solve"] / g.seconds,
+            "E_S_gpu_minus_oracle": g.E_S - o["E_S"], "E_T_gpu_minus_oracle": g.E_T - o["E_T"]}
 
 
 def main():
@@ -170,6 +297,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the mixed-vs-FP64 solves")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,26 +345,23 @@ def main():
     prof = L.dcsd_profile(eng.ctx, 0, 0)
     launches = eng.launches() - launches0
     t_step = reduce_max(dist, ms / 1e3 / args.steps, "cuda")
-    # end-to-end: residual through the C ABI with pinned host buffers
+    # end-to-end: the same iteration through the C ABI with pinned host
+    # buffers -- dcsd_solve with mem_kind HOST and maxiter 1 copies the
+    # amplitudes in, runs one residual and update, and copies them out
     Th = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in T]
-    Rh = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in T]
     for a, b in zip(Th, T):
         a.copy_(b.cpu())
-    lib = L.load()
-    import ctypes as C
-    Wc, Ec = C.c_double(), C.c_double()
+    eng.reserve(prec, diis_n=8, host_staging=True)
+    e2e_opts = L.dcsd_solve_opts(P.DCSD, 0, prec, 1, 8, 1e-30, 1e-5, 1, 0.0)
 
-    def host_residual():
-        st = lib.dcsd_residual(eng.ctx, 0, P.DCSD, prec, L.MEM_HOST, *[x.data_ptr() for x in Th],
-                               *[x.data_ptr() for x in Rh], C.byref(Wc), C.byref(Ec))
-        if st != 0:
-            raise RuntimeError(lib.dcsd_last_error(eng.ctx))
-    host_residual()
+    def host_iteration():
+        L.dcsd_solve(eng.ctx, e2e_opts, L.MEM_HOST, [x.data_ptr() for x in Th])
+    host_iteration()
     barrier()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        host_residual()
+        host_iteration()
     barrier()
     e2e = whole_job_value(reduce_max(dist, (time.perf_counter() - t0) / e2e_steps, "cuda"), world)
     nbytes = int(sum(x.numel() * 8 for x in Th))
@@ -267,21 +392,31 @@ def main():
                      "traffic_unit": "bytes per ladder launch (producer or consumer), DRAM read + write"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                "note": "dcsd_residual with pinned host buffers (copies in the timed region)"},
+                "note": "dcsd_solve(maxiter 1) with pinned host amplitudes: copy in, residual, update, copy out"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "last_residual": {"max_r": res.max_r, "dEA": res.dEA, "W": res.W},
     }
+    eng.close()
+    del T, Th
     if rank == 0:
         print("# gpu part: " + json.dumps(line), file=sys.stderr, flush=True)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_extra:
         try:
-            line["cpu_baseline"] = oracle_sample(seconds_budget=15.0)
+            line["mixed_vs_fp64"] = mixed_vs_fp64(P)
+        except Exception as ex:
+            line["mixed_vs_fp64"] = {"error": repr(ex)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_sample(args.config)
         except Exception as ex:  # the GPU measurement stands without it
             line["cpu_baseline"] = {"value": None, "error": repr(ex)}
+        try:
+            line["cpu_baseline_same_config"] = same_config_c1(P)
+        except Exception as ex:
+            line["cpu_baseline_same_config"] = {"error": repr(ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    eng.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

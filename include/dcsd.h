@@ -408,6 +408,84 @@ dcsd_status dcsd_energy_noalloc(int n_c, int n_v, int naux, int ref,
                                 const double* T2bb, const double* T2ab,
                                 double* dEA, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * FCIDUMP input.  The paper's calculations read their integrals from
+ * FCIDUMP files written after the ROHF or 2D-SCF step (Section III,
+ * computational details).  Format: the namelist header &FCI NORB, NELEC,
+ * MS2, ORBSYM, ISYM &END, then lines "value i j k l" (1-based): (ij|kl)
+ * (chemists' notation, one of the eight equivalent permutations), h_ij
+ * (k = l = 0), orbital energies (j = k = l = 0, ignored) and the core
+ * energy (all zero).  Spin-restricted orbitals only (IUHF files are
+ * refused).  The host code keeps the four-index integrals as a dense array,
+ * so NORB is limited to 160.  The open-shell determinant Phi_A doubly
+ * occupies the first (NELEC - 2) / 2 orbitals and singly occupies the next
+ * two, t (alpha) and u (beta); MS2 must be 0.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int norb, nelec, ms2;     /* from the header                                 */
+    int n_frozen;             /* frozen core orbitals folded into h              */
+    int n_c, n_v, naux;       /* dimensions of the context (naux = Cholesky rank) */
+    double e_core;            /* core energy incl. the frozen-core contribution  */
+    double e_ref;             /* <Phi_A|H|Phi_A>, total reference energy         */
+    double chol_max_error;    /* bound on |(pq|rs) - sum_L B_pq^L B_rs^L|        */
+} dcsd_fcidump_info;
+
+/* dcsd_fcidump_header -- NORB, NELEC and MS2 of an FCIDUMP file (host).
+ * Errors: INVALID_ARG (NULL pointer, unreadable file, no &FCI header, NORB
+ * outside 1..160, IUHF file); dcsd_fcidump_error() has the message. */
+dcsd_status dcsd_fcidump_header(const char* path, int* norb, int* nelec, int* ms2);
+
+/* dcsd_fcidump_read -- the integrals of an FCIDUMP file (host):
+ *   h     : out, [norb][norb] one-electron integrals, symmetric;
+ *   eri   : out, [norb]^4 two-electron integrals (pq|rs) with all eight
+ *           permutations of every listed element filled; absent ones 0;
+ *   ecore : out, the core energy.
+ * norb must equal the header's NORB.  Errors: INVALID_ARG (as above, a
+ * malformed line, an index outside 0..NORB). */
+dcsd_status dcsd_fcidump_read(const char* path, int norb, double* h, double* eri, double* ecore);
+
+/* dcsd_cholesky_host -- pivoted Cholesky factorisation of the integral
+ * matrix V[(pq),(rs)] = (pq|rs) (Beebe and Linderberg, 1977; host): factors
+ * B[L][p][q], L < *rank, with |(pq|rs) - sum_L B^L_pq B^L_rs| <= tol for
+ * every element.  The paper uses full four-index integrals; this exact
+ * factorisation lets them enter the engine in the factorised form its
+ * kernels use in place of density fitting.
+ *   n        : orbitals (<= 160); eri : [n]^4 (pq|rs), symmetric as above.
+ *   tol      : threshold on the remaining diagonal, > 0 (e.g. 1e-12).
+ *   max_rank : capacity of B in factors (n (n + 1) / 2 always suffices).
+ *   B        : out, [max_rank][n][n].  rank : out.  max_diag_left : out or
+ *              NULL, the largest remaining diagonal element (the error bound).
+ * Errors: INVALID_ARG. */
+dcsd_status dcsd_cholesky_host(int n, const double* eri, double tol, int max_rank, double* B, int* rank,
+                               double* max_diag_left);
+
+/* dcsd_fcidump_prepare -- everything dcsd_init needs from an FCIDUMP file
+ * (host): frozen-core folding of the first n_frozen orbitals into h and the
+ * core energy, the Fock matrices of Phi_A over the correlated orbitals,
+ * f^s_pq = h'_pq + sum_{k in Phi_A} [(pq|kk) - delta(s_k, s) (pk|kq)], the
+ * Cholesky factors of the correlated integrals (threshold chol_tol) and the
+ * reference energy.  Call first with NULL arrays to learn the sizes in
+ * *info (n = n_c + 2 + n_v, naux), then with fock_a, fock_b [n][n] and B
+ * [naux][n][n].  Errors: INVALID_ARG (file errors as above, MS2 != 0, odd
+ * NELEC, n_frozen outside 0..(NELEC-2)/2, no virtual orbital). */
+dcsd_status dcsd_fcidump_prepare(const char* path, int n_frozen, double chol_tol, dcsd_fcidump_info* info,
+                                 double* fock_a, double* fock_b, double* B);
+
+/* dcsd_init_fcidump -- dcsd_fcidump_prepare followed by dcsd_init (host
+ * inputs) on `stream`.  stored_ladder 1 also keeps the four-index (ac|bd)
+ * of the virtual orbitals (t, u and the external ones) on the device, and
+ * the FP64 residual then takes its particle-particle ladder from them
+ * instead of from the factors (a check of the factorised ladder; the
+ * tensor-core precisions and the reverse mode always use the factors).
+ * info : out or NULL.  Errors: those of both calls; OOM for the stored
+ * integrals. */
+dcsd_status dcsd_init_fcidump(dcsd_ctx** out, const char* path, int n_frozen, double chol_tol, int stored_ladder,
+                              void* stream, dcsd_fcidump_info* info);
+
+/* dcsd_fcidump_error -- message of the last failed FCIDUMP call (host,
+ * process-wide). */
+const char* dcsd_fcidump_error(void);
+
 #ifdef __cplusplus
 }
 #endif

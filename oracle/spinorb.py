@@ -28,7 +28,7 @@ ALPHA, BETA = 0, 1
 
 
 class Frame:
-    def __init__(self, n_c, n_v, B, fock_a, fock_b, ref):
+    def __init__(self, n_c, n_v, B, fock_a, fock_b, ref, eri=None):
         self.n_c, self.n_v, self.ref = n_c, n_v, ref
         self.n = n_c + 2 + n_v
         self.o, self.v = n_c + 1, n_v + 1
@@ -38,6 +38,7 @@ class Frame:
         self.vir_sp = np.array(va + vb)
         self.vir_spin = np.array([ALPHA] * len(va) + [BETA] * len(vb))
         self.B = B
+        self.eri = eri  # four-index (pq|rs) used instead of B when given
         fa, fb = (fock_a, fock_b) if ref == 0 else (fock_b, fock_a)
         self.fock = (fa, fb)
         self._cache = {}
@@ -59,9 +60,12 @@ class Frame:
     def _coul(self, k1, k2, k3, k4):
         """<pq|rs> = (pr|qs) d(s_p,s_r) d(s_q,s_s) for p in k1, q in k2, r in k3, s in k4."""
         (p, ps), (q, qs), (r, rs), (s, ss) = (self.space(k) for k in (k1, k2, k3, k4))
-        Bpr = self.B[:, p][:, :, r]
-        Bqs = self.B[:, q][:, :, s]
-        g = np.einsum("Lpr,Lqs->pqrs", Bpr, Bqs, optimize=True)
+        if self.eri is not None:
+            g = self.eri[np.ix_(p, r, q, s)].transpose(0, 2, 1, 3).copy()
+        else:
+            Bpr = self.B[:, p][:, :, r]
+            Bqs = self.B[:, q][:, :, s]
+            g = np.einsum("Lpr,Lqs->pqrs", Bpr, Bqs, optimize=True)
         g *= (ps[:, None] == rs[None, :])[:, None, :, None]
         g *= (qs[:, None] == ss[None, :])[None, :, None, :]
         return g
@@ -84,9 +88,12 @@ class Frame:
         """<ab||ef> for the virtual indices a in a_idx (all b, e, f)."""
         (v, vs) = self.space("v")
         pa, psa = v[a_idx], vs[a_idx]
-        Bae = self.B[:, pa][:, :, v]
-        Bbf = self.B[:, v][:, :, v]
-        g1 = np.einsum("Lae,Lbf->abef", Bae, Bbf, optimize=True)
+        if self.eri is not None:
+            g1 = self.eri[np.ix_(pa, v, v, v)].transpose(0, 2, 1, 3).copy()
+        else:
+            Bae = self.B[:, pa][:, :, v]
+            Bbf = self.B[:, v][:, :, v]
+            g1 = np.einsum("Lae,Lbf->abef", Bae, Bbf, optimize=True)
         g1 *= (psa[:, None] == vs[None, :])[:, None, :, None]
         g1 *= (vs[:, None] == vs[None, :])[None, :, None, :]
         g2 = g1.transpose(0, 1, 3, 2)

@@ -299,8 +299,9 @@ def c_other(fr: Frame, fro: Frame, t1o, t2o):
 # ----------------------------------------------------------------------------
 
 def frames(sys, ref):
-    fr = Frame(sys.n_c, sys.n_v, sys.B, sys.fock_a, sys.fock_b, ref)
-    fro = Frame(sys.n_c, sys.n_v, sys.B, sys.fock_a, sys.fock_b, 1 - ref)
+    eri = getattr(sys, "eri", None)
+    fr = Frame(sys.n_c, sys.n_v, sys.B, sys.fock_a, sys.fock_b, ref, eri=eri)
+    fro = Frame(sys.n_c, sys.n_v, sys.B, sys.fock_a, sys.fock_b, 1 - ref, eri=eri)
     return fr, fro
 
 

@@ -57,6 +57,24 @@ class Engine:
     def from_system(cls, s, **kw):
         return cls(s.n_c, s.n_v, s.naux, s.fock_a, s.fock_b, s.B, **kw)
 
+    @classmethod
+    def from_fcidump(cls, path, n_frozen=0, chol_tol=1e-12, stored_ladder=False, stream=None):
+        """Context from an FCIDUMP file (dcsd_init_fcidump): frozen-core
+        folding, Fock matrices of Phi_A and Cholesky factors are prepared by
+        the library; .fcidump holds its dcsd_fcidump_info (dimensions,
+        reference energy e_ref for total energies)."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ctx, info = L.dcsd_init_fcidump(path, n_frozen, chol_tol, stored_ladder, self.stream.cuda_stream)
+        self.fcidump = info
+        self.n_c, self.n_v, self.naux = info.n_c, info.n_v, info.naux
+        self.o, self.v = self.n_c + 1, self.n_v + 1
+        self._inputs = None
+        return self
+
     # -- layout helpers --------------------------------------------------
     def shapes(self):
         o, v = self.o, self.v
@@ -148,6 +166,8 @@ class Engine:
         was created with, as leaves for residual_autograd (their gradients
         are the Fock-matrix and DF-factor parts of dcsd_vjp).  Modifying them
         does not change the engine: the library keeps its own copy."""
+        if self._inputs is None:
+            raise ValueError("this engine was not created from in-memory inputs")
         for x in self._inputs:
             x.requires_grad_(requires_grad)
         return self._inputs

@@ -24,7 +24,9 @@ PREC_FP64, PREC_BF16, PREC_BF16X3, PREC_MIXED, PREC_BF16X6 = 0, 1, 2, 3, 4
 EXPORTS = ["dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff",
            "dcsd_destroy", "dcsd_last_error", "dcsd_kernel_launches", "dcsd_profile",
            "dcsd_energy_noalloc", "dcsd_selftest_conversions", "dcsd_vjp", "dcsd_lambda",
-           "dcsd_coupling_host", "dcsd_einsum_host", "dcsd_reserve"]
+           "dcsd_coupling_host", "dcsd_einsum_host", "dcsd_reserve", "dcsd_fcidump_header",
+           "dcsd_fcidump_read", "dcsd_cholesky_host", "dcsd_fcidump_prepare", "dcsd_init_fcidump",
+           "dcsd_fcidump_error"]
 PROF_CLASSES = ["ladder_tc", "tc_other", "pack", "fp64", "c4", "c5", "c6", "c7"]
 
 
@@ -43,6 +45,12 @@ class dcsd_result(C.Structure):
                 ("E_T", C.c_double), ("max_r", C.c_double), ("iters", C.c_int),
                 ("converged", C.c_int), ("seconds", C.c_double), ("switched_at", C.c_int),
                 ("polished_at", C.c_int)]
+
+
+class dcsd_fcidump_info(C.Structure):
+    _fields_ = [("norb", C.c_int), ("nelec", C.c_int), ("ms2", C.c_int), ("n_frozen", C.c_int),
+                ("n_c", C.c_int), ("n_v", C.c_int), ("naux", C.c_int), ("e_core", C.c_double),
+                ("e_ref", C.c_double), ("chol_max_error", C.c_double)]
 
 
 class DcsdError(RuntimeError):
@@ -92,6 +100,17 @@ def load():
     lib.dcsd_einsum_host.restype = C.c_int
     lib.dcsd_reserve.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.dcsd_reserve.restype = C.c_int
+    lib.dcsd_fcidump_header.argtypes = [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.dcsd_fcidump_read.argtypes = [C.c_char_p, C.c_int, P, P, D]
+    lib.dcsd_cholesky_host.argtypes = [C.c_int, P, C.c_double, C.c_int, P, C.POINTER(C.c_int), D]
+    lib.dcsd_fcidump_prepare.argtypes = [C.c_char_p, C.c_int, C.c_double, C.POINTER(dcsd_fcidump_info), P, P, P]
+    lib.dcsd_init_fcidump.argtypes = [C.POINTER(P), C.c_char_p, C.c_int, C.c_double, C.c_int, P,
+                                      C.POINTER(dcsd_fcidump_info)]
+    lib.dcsd_fcidump_error.argtypes = []
+    lib.dcsd_fcidump_error.restype = C.c_char_p
+    for name in ("dcsd_fcidump_header", "dcsd_fcidump_read", "dcsd_cholesky_host", "dcsd_fcidump_prepare",
+                 "dcsd_init_fcidump"):
+        getattr(lib, name).restype = C.c_int
     for name in ("dcsd_init", "dcsd_residual", "dcsd_energy", "dcsd_solve", "dcsd_heff", "dcsd_destroy"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -239,3 +258,64 @@ def dcsd_lambda(ctx, opts, state, mem_kind, T, Lam, rdm_a=None, rdm_b=None):
     if st not in (0, 4):
         _check(st, ctx)
     return res
+
+
+def _fcidump_check(st):
+    if st != DCSD_OK:
+        raise DcsdError(st, load().dcsd_fcidump_error().decode(errors="replace"))
+
+
+def dcsd_fcidump_header(path):
+    """(norb, nelec, ms2) of an FCIDUMP file."""
+    n, ne, ms = C.c_int(), C.c_int(), C.c_int()
+    _fcidump_check(load().dcsd_fcidump_header(os.fsencode(path), C.byref(n), C.byref(ne), C.byref(ms)))
+    return n.value, ne.value, ms.value
+
+
+def dcsd_fcidump_read(path):
+    """(h [n,n], eri [n,n,n,n], ecore) as numpy arrays, read by the library."""
+    import numpy as np
+    n, _, _ = dcsd_fcidump_header(path)
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    ec = C.c_double()
+    _fcidump_check(load().dcsd_fcidump_read(os.fsencode(path), n, h.ctypes.data, eri.ctypes.data, C.byref(ec)))
+    return h, eri, ec.value
+
+
+def dcsd_cholesky_host(eri, tol=1e-12):
+    """Pivoted Cholesky factors B [rank, n, n] of (pq|rs) and the bound on the
+    remaining error."""
+    import numpy as np
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    n = eri.shape[0]
+    cap = n * (n + 1) // 2
+    B = np.zeros((cap, n, n))
+    r, left = C.c_int(), C.c_double()
+    st = load().dcsd_cholesky_host(n, eri.ctypes.data, tol, cap, B.ctypes.data, C.byref(r), C.byref(left))
+    if st != DCSD_OK:
+        raise DcsdError(st, "dcsd_cholesky_host failed")
+    return B[:r.value].copy(), left.value
+
+
+def dcsd_fcidump_prepare(path, n_frozen=0, chol_tol=1e-12):
+    """(info, fock_a, fock_b, B) as prepared by the library for dcsd_init."""
+    import numpy as np
+    info = dcsd_fcidump_info()
+    p = os.fsencode(path)
+    _fcidump_check(load().dcsd_fcidump_prepare(p, n_frozen, chol_tol, C.byref(info), None, None, None))
+    n = info.n_c + 2 + info.n_v
+    fa, fb = np.zeros((n, n)), np.zeros((n, n))
+    B = np.zeros((info.naux, n, n))
+    _fcidump_check(load().dcsd_fcidump_prepare(p, n_frozen, chol_tol, C.byref(info), fa.ctypes.data,
+                                               fb.ctypes.data, B.ctypes.data))
+    return info, fa, fb, B
+
+
+def dcsd_init_fcidump(path, n_frozen, chol_tol, stored_ladder, stream):
+    """Create a context from an FCIDUMP file; returns (ctx, info)."""
+    ctx = C.c_void_p()
+    info = dcsd_fcidump_info()
+    _fcidump_check(load().dcsd_init_fcidump(C.byref(ctx), os.fsencode(path), n_frozen, chol_tol,
+                                            1 if stored_ladder else 0, stream, C.byref(info)))
+    return ctx, info

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdcsd.so")
-UNITS = ["gemm64", "mterm", "residual", "api", "tc_gemm", "noalloc", "selftest", "vjp"]
+UNITS = ["gemm64", "mterm", "residual", "api", "tc_gemm", "noalloc", "selftest", "vjp", "fcidump"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

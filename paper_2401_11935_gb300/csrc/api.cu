@@ -213,6 +213,8 @@ void free_ctx(Ctx* c) {
     }
     c->t2 = nullptr;
     c->R2 = nullptr;
+    if (c->vvvv) cudaFree(c->vvvv);
+    c->vvvv = nullptr;
     if (c->r2f) cudaFree(c->r2f);
     c->r2f = nullptr;
     if (c->hostbuf) cudaFreeHost(c->hostbuf);

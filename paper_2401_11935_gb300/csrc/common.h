@@ -193,6 +193,10 @@ struct Ctx {
     double* jac_s = nullptr;      // [len] Jacobi step and new amplitudes when no DIIS history is kept
     double* jac_t = nullptr;
     double* defect = nullptr;     // [len] MIXED solve: defect e = R_X6(T) - R64(T) of the last outer step
+    // stored four-index integrals (ac|bd) of the union virtuals, [a][c][b][d]
+    // (contexts made from FCIDUMP with the stored-integral ladder); the FP64
+    // residual then takes its particle-particle ladder from them
+    double* vvvv = nullptr;
 };
 
 // ---------------------------------------------------------------------------

@@ -122,6 +122,18 @@ dcsd_status merge_r2f(Ctx* c) {
     return launch_check(c, "merge_r2f");
 }
 
+dcsd_status set_vvvv(Ctx* c, const double* host_vvvv) {
+    const size_t V = c->V, nv4 = V * V * V * V;
+    if (!c->vvvv && cudaMalloc((void**)&c->vvvv, nv4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->vvvv = nullptr;
+        c->err = "cudaMalloc of the stored (ac|bd) integrals failed";
+        return DCSD_ERR_OOM;
+    }
+    DCSD_CUDA(c, cudaMemcpy(c->vvvv, host_vvvv, nv4 * sizeof(double), cudaMemcpyHostToDevice));
+    return DCSD_OK;
+}
+
 dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
     const double x = method_dc(method) ? 0.0 : 1.0;
@@ -292,9 +304,15 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         c->rec = rec;
         DCSD_TRY(st);
     } else {
-        // FP64: chunked einsums (while recording, one tape entry each)
+        // FP64: chunked einsums (while recording, one tape entry each), or,
+        // with stored four-index integrals, one contraction with them (the
+        // reverse mode records the factorised form, equal to the threshold
+        // of the factorisation)
         const long ch = std::max<long>(1, std::min<long>(V, (long)(c->big_elems / (V * V * V))));
-        DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, 0));
+        if (c->vvvv && !c->rec)
+            DCSD_TRY(einsum64(c, "sijcd,acbd->sijab", 1.0, t2, view(c->vvvv, {V, V, V, V}), 1.0, R2));
+        else
+            DCSD_TRY(ladder64(c, t2, Bvv, R2, c->big0, ch, 0));
         // T1 corrections: G[s][ij][k][b] = sum_cd (kc|bd) t_s[ij][cd]; G[3] with
         // t_ab transposed in (c,d); H[s][ij][k][m] = sum_cd (kc|md) t_s[ij][cd]
         const long kc = std::max<long>(1, std::min<long>(O, (long)(c->big_elems / (V * V * V))));

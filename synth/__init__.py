@@ -57,6 +57,7 @@ class System:
     fock_a: np.ndarray     # [n, n] Fock matrix of alpha spin w.r.t. Phi_A
     fock_b: np.ndarray     # [n, n] Fock matrix of beta spin w.r.t. Phi_A
     h: np.ndarray | None = None  # [n, n] core Hamiltonian (pin systems only)
+    eri: np.ndarray | None = None  # [n, n, n, n] four-index (pq|rs), when given instead of factors
 
     @property
     def n(self):

@@ -15,10 +15,41 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
+import dataclasses  # noqa: E402
+
+import numpy as np  # noqa: E402
+
 from synth import CONFIGS, CONFIG_SEED, b_sigma_for, make_system  # noqa: E402
 from oracle import solve  # noqa: E402
 
 TOL = {"c1": 1e-10, "c2": 1e-10, "c3": 1e-9, "c4": 1e-10}
+
+
+def response_direction(s, method):
+    """Seeded symmetric Fock perturbation (df_alpha, df_beta), N(0, 0.01^2)
+    entries, zero where the orbital Z2 labels differ (the perturbed system
+    keeps the symmetry of the unperturbed one)."""
+    rng = np.random.default_rng(17 + method)
+    mask = (s.parity[:, None] == s.parity[None, :]).astype(float)
+
+    def sym(x):
+        return 0.5 * (x + x.T) * mask
+    return sym(rng.normal(0, 1e-2, s.fock_a.shape)), sym(rng.normal(0, 1e-2, s.fock_b.shape))
+
+
+def response(s, method, tol, h=0.05):
+    """d E_S / de and d E_T / de of the converged 2D energies along
+    f -> f + e df (fourth-order central stencil of four oracle solves)."""
+    dfa, dfb = response_direction(s, method)
+    E = {}
+    for e in (-2 * h, -h, h, 2 * h):
+        sp = dataclasses.replace(s, fock_a=s.fock_a + e * dfa, fock_b=s.fock_b + e * dfb)
+        _, info = solve.solve(sp, method, ref=0, tol=tol, maxiter=300)
+        assert info["converged"]
+        E[e] = (info["E_S"], info["E_T"])
+    d = [(8 * (E[h][k] - E[-h][k]) - (E[2 * h][k] - E[-2 * h][k])) / (12 * h) for k in (0, 1)]
+    return {"h": h, "direction_seed": 17 + method, "direction_abs_sum": float(np.abs(dfa).sum() + np.abs(dfb).sum()),
+            "dE_S": d[0], "dE_T": d[1]}
 
 
 def main(names):
@@ -44,6 +75,11 @@ def main(names):
                 out["results"][key]["converged"] = bool(info["converged"])
                 out["results"][key]["oracle_seconds"] = time.time() - t0
                 print(name, key, out["results"][key], flush=True)
+        if name == "c1":
+            out["response"] = {}
+            for method, mname in ((0, "2D-CCSD"), (1, "2D-DCSD")):
+                out["response"][mname] = response(s, method, 1e-12)
+                print(name, "response", mname, out["response"][mname], flush=True)
         with open(os.path.join(HERE, f"{name}_energies.json"), "w") as f:
             json.dump(out, f, indent=1)
 

@@ -129,9 +129,10 @@ def test_reserve_then_no_device_allocation(P):
 def test_reserve_rejects_bad_arguments(P):
     s = make_system((1, 2, 4), seed=1)
     eng = P.Engine.from_system(s)
-    for args in ((9, 8, 0), (0, 17, 0), (0, 8, 2)):
+    from paper_2401_11935_gb300 import _lib as L
+    for args in ((9, 8, 0), (0, 17, 0), (0, 8, 2), (0, -1, 0)):
         with pytest.raises(P.DcsdError) as e:
-            eng.reserve(args[0], diis_n=args[1], host_staging=args[2])
+            L.dcsd_reserve(eng.ctx, *args)
         assert e.value.status == 1
     eng.close()
 
