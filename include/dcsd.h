@@ -27,10 +27,15 @@
  *     T2aa, T2bb [o][o][v][v]   antisymmetric in (i,j) and in (a,b)
  *     T2ab      [o][o][v][v]    (alpha occ i, beta occ j, alpha vir a, beta vir b).
  * The excitation Phi_ref -> the other determinant is T2ab[o-1][o-1][0][0]
- * in both frames; for the 2D methods its amplitude must be zero (Section
- * II, text after Eq. 4); for the fixed-reference methods the library uses
- * the fixed value (+1 or -1) there, whatever the array holds, and returns
- * that value in solved amplitudes.
+ * in both frames.  It is not a free amplitude, and the library sets it
+ * whatever the array holds (and returns that value in solved amplitudes):
+ * for the 2D methods by the C-condition <other|exp(T)|ref> = 0 of the
+ * two-determinant wave operator, i.e. to -T1a[o-1][0] * T1b[o-1][0] (the
+ * internal singles t alpha -> u alpha and u beta -> t beta of frame A, their
+ * flips in frame B), which is zero in the CAS case (t and u in different
+ * irreps, Section II, text after Eq. 4) and not in the IAS case (same
+ * irrep); for the fixed-reference methods to the fixed value (+1 or -1).
+ * Its gradient in dcsd_vjp is zero; the derivative flows to the singles.
  * Fock matrices passed to dcsd_init are those of Phi_A; for ref = 1 the
  * library uses the alpha matrix as beta and vice versa (spin flip).
  *
@@ -182,8 +187,10 @@ dcsd_status dcsd_reserve(dcsd_ctx* ctx, int precision, int diis_n, int host_stag
 
 /* dcsd_residual -- one evaluation of the 2D residual (Eqs. 3-4).
  *   R = R^X(T) + M W with R^X the CCSD (method 0) or DCSD (method 1)
- *   single-reference residual; W = R^X at the A->B double; that element of
- *   R2ab is returned as zero.  dEA receives Delta E_A (Eq. 2).
+ *   single-reference residual; W = <B|H_N exp(T_A)|A>, which is R^X at the
+ *   A->B double plus the products of the two internal singles with their
+ *   R^X elements (zero in the CAS case); that element of R2ab is returned
+ *   as zero.  dEA receives Delta E_A (Eq. 2).
  *   Fixed-reference methods (2..5): R = R^X(T) with the A->B amplitude at
  *   its fixed value and no M W terms; W receives R^X at the fixed
  *   excitation (not an equation of the method), whose R2ab element is

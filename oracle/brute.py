@@ -166,8 +166,9 @@ class Brute:
         return project_singles_doubles(self.space, fr, det, w)
 
     def twod(self, ref, t1, t2, t1o, t2o):
-        """Omega1, Omega2 (Bloch form), c^A, c^B, W := R^CC of the A->B
-        double, dE_A, and the residuals R1 = Omega1, R2 = Omega2 - A[t1 Omega1]."""
+        """Omega1, Omega2 (Bloch form), c^A, c^B, W = <B|H_N exp(T_A)|A>,
+        dE_A, and the residuals R1 = Omega1, R2 = Omega2 - A[t1 Omega1].  The
+        amplitudes must satisfy the C-condition <B|exp(T_A)|A> = 0."""
         fr, fro = self.frame(ref), self.frame(1 - ref)
         detA, detB = frame_det(fr), frame_det(fro)
         xA = self.space.vec(detA)
@@ -181,7 +182,9 @@ class Brute:
         hbar = expm_apply(-TA, hN)
         i, j, a, b = fr.q_ab()
         d, s = excited(fr, detA, [i, j], [a, b], self.space.n)
-        W = s * hbar[self.space.index[d]]
+        # W = <B| H_N exp(T_A) |A> (the Bloch effective Hamiltonian with
+        # intermediate normalisation, <B|exp(T_A)|A> = 0)
+        W = s * hN[self.space.index[d]]
         h1, h2 = project_singles_doubles(self.space, fr, detA, hN)
         cA1, cA2 = project_singles_doubles(self.space, fr, detA, eA)
         cB1, cB2 = project_singles_doubles(self.space, fr, detA, eB)

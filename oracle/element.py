@@ -168,6 +168,7 @@ class ElementOracle:
         self.fr, self.fro = twod.frames(sys, ref)
         fr = self.fr
         self.o, self.v = fr.o, fr.v
+        T = twod.c_condition(T)
         self.T = Amplitudes(fr, T)
         self.To = Amplitudes(fr, flip_abi(T))  # T_other in this frame's ABI layout
         self.t1 = self.T.t1
@@ -412,9 +413,17 @@ class ElementOracle:
         return e
 
     def W(self):
-        """W: the connected (DC) residual element of the A->B double."""
+        """W = <B|H_N exp(T_A)|A>: the connected (DC) residual element of the
+        A->B double plus A(ij;ab)[t_ia R^X_jb] there (the internal-singles
+        products, zero in the CAS case; ``twod.residual_so``)."""
         if self._W is None:
-            self._W = self.r2x(*self.fr.q_ab())
+            i, j, a, b = self.fr.q_ab()
+            t1 = self.t1
+            w = self.r2x(i, j, a, b)
+            for (p, q, r, u, sg) in ((i, a, j, b, 1.0), (j, b, i, a, 1.0), (j, a, i, b, -1.0), (i, b, j, a, -1.0)):
+                if t1[p, q] != 0.0:
+                    w += sg * t1[p, q] * self.r1x(r, u)
+            self._W = w
         return self._W
 
     # --- the 2D residual -----------------------------------------------------------

@@ -111,6 +111,8 @@ def solve(sys, method, ref=0, tol=1e-10, maxiter=200, diis_n=8, T0=None, verbose
     if fixed is not None:
         info.update(E=info["dEA"], converged=info["max_r"] <= tol)
         return T, info
+    from .twod import c_condition
+    T = c_condition(T)
     H, ev, si = heff(info["dEA"], info["W"])
     info.update(E_S=info["dEA"] + info["W"], E_T=info["dEA"] - info["W"], H=H, evals=ev,
                 singlet_index=si, converged=info["max_r"] <= tol)

@@ -15,8 +15,10 @@ Eqs. 3/4) this reads, for singles and doubles,
   R2_ijab = R^CC_ijab - W ( c^B_ijab - A(ij;ab)[ t_ia c^B_jb ] ),
 
 the M*W renormalisation terms of Eqs. 3-4 (R2 = Omega2 - A[t1 Omega1]).
-The A->B doubles amplitude is held at zero, W is the residual element of
-that excitation and the element itself is then zeroed (text after Eq. 4).
+The A->B doubles amplitude is fixed by the C-condition (``c_condition``:
+zero in the CAS case, as the text after Eq. 4 states), W = <B|H_N e^{T_A}|A>
+is the residual element of that excitation (plus the internal-singles
+products of the IAS case) and the element itself is then zeroed.
 T_B is T_A with alpha and beta exchanged (Section II).  The coefficients
 c^B_q are evaluated exactly by cluster-to-CI algebra on determinants, so no
 term with a spin-orbital occurring twice can arise (the omission the paper
@@ -305,13 +307,47 @@ def frames(sys, ref):
     return fr, fro
 
 
+def c_condition(T):
+    """ABI amplitudes with the A->B doubles element fixed by the C-condition.
+
+    Intermediate normalisation of the Jeziorski-Monkhorst wave operator
+    requires <other| exp(T) |this> = 0.  That coefficient is the A->B doubles
+    amplitude plus the product of the two internal singles t alpha -> u
+    alpha and u beta -> t beta (sign +1 in both frames, checked with CI
+    vectors), so the element equals -T1a[o-1,0] T1b[o-1,0].  In the CAS case
+    of Section II the internal singles vanish by symmetry and the element is
+    zero, as the paper states; in the IAS case they do not (Section II: the
+    terms with the all-internal singles have to be included)."""
+    T = tuple(np.array(x, dtype=float) for x in T)
+    o = T[0].shape[0]
+    T[4][o - 1, o - 1, 0, 0] = -T[0][o - 1, 0] * T[1][o - 1, 0]
+    return T
+
+
+def _c_condition_so(fr, t1, t2):
+    i, j, a, b = fr.q_ab()
+    t2 = t2.copy()
+    val = -t1[i, a] * t1[j, b]
+    t2[i, j, a, b], t2[j, i, a, b], t2[i, j, b, a], t2[j, i, b, a] = val, -val, -val, val
+    return t2
+
+
 def residual_so(fr, fro, method, t1, t2, t1o, t2o):
-    """Spin-orbital 2D residual; returns (R1, R2, W, dE_A, R1cc, R2cc)."""
+    """Spin-orbital 2D residual; returns (R1, R2, W, dE_A, R1cc, R2cc).  The
+    A->B element of t2 and t2o is set by the C-condition first.
+
+    W = <B| H_N exp(T_A) |A> = R^X_AB + A(ij;ab)[t_ia R^X_jb] at the A->B
+    double (and + c^A_AB dE_A, zero by the C-condition): the residual element
+    of the text after Eq. 4, plus the internal-singles products that the IAS
+    case adds (zero in the CAS case)."""
+    t2 = _c_condition_so(fr, t1, t2)
+    t2o = _c_condition_so(fro, t1o, t2o)
     R1x, R2x = ccsd.ccsd_residual(fr, t1, t2)
     if method == DCSD:
         R2x = R2x + ccsd.dc_delta(fr, t2)
     i, j, a, b = fr.q_ab()
-    W = R2x[i, j, a, b]
+    W = (R2x[i, j, a, b] + t1[i, a] * R1x[j, b] - t1[j, a] * R1x[i, b] - t1[i, b] * R1x[j, a]
+         + t1[j, b] * R1x[i, a])
     c1, c2 = c_other(fr, fro, t1o, t2o)
     tc = np.einsum("ia,jb->ijab", t1, c1)
     tc = ccsd.P_ij(ccsd.P_ab(tc))
@@ -328,6 +364,7 @@ def residual(sys, ref, method, T):
     to Phi_A (ref 0) or Phi_B (ref 1).  Returns (R, W, dE_A) with R in the
     same layout."""
     fr, fro = frames(sys, ref)
+    T = c_condition(T)
     t1, t2 = unpack(fr.o, fr.v, T)
     t1o, t2o = unpack(fr.o, fr.v, flip_abi(T))
     R1, R2, W, dE, _, _ = residual_so(fr, fro, method, t1, t2, t1o, t2o)

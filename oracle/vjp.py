@@ -17,8 +17,9 @@ unit direction of the stored amplitude arrays (tiny systems only).
 
 The same-spin doubles are antisymmetric and B and f are symmetric, so only
 derivatives along directions with those symmetries are defined independently
-of how an implementation reads the stored arrays; ``project`` maps a
-gradient onto that subspace for comparisons.
+of how an implementation reads the stored arrays; the A->B doubles element
+is set by the C-condition (``twod.c_condition``), so the derivative along it
+is zero; ``project`` maps a gradient onto that subspace for comparisons.
 """
 from __future__ import annotations
 
@@ -73,5 +74,9 @@ def antisym(x):
 
 def project(G):
     """Gradient along symmetry-respecting directions: same-spin doubles
-    antisymmetrised, everything else unchanged."""
-    return (G[0], G[1], antisym(G[2]), antisym(G[3]), G[4])
+    antisymmetrised, the A->B doubles element (fixed by the C-condition, not
+    a free amplitude) zero, everything else unchanged."""
+    G4 = np.array(G[4], dtype=float)
+    o = G4.shape[0]
+    G4[o - 1, o - 1, 0, 0] = 0.0
+    return (G[0], G[1], antisym(G[2]), antisym(G[3]), G4)

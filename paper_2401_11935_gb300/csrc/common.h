@@ -76,11 +76,14 @@ enum TapeOpType {
     OP_SWAPVIR,  // t2s = t2 with the virtual pair exchanged
     OP_MTERMS,   // two-determinant coupling terms, iarg[0] = ref
     OP_LADDER,   // R2 += sum_cd t2 (ac|bd), integrals rebuilt in the reverse sweep
-    OP_GPASS     // G = sum_cd t2 (kc|bd), integrals rebuilt in the reverse sweep
+    OP_GPASS,    // G = sum_cd t2 (kc|bd), integrals rebuilt in the reverse sweep
+    OP_CCOND,    // t2[e] = -t1[p] t1[q] (C-condition; iarg: e, p, q as longs in p[])
+    OP_WFULL     // W = R2[e] + t1[p] R1[q] + t1[q] R1[p] (R1 values saved in scal[50..51])
 };
 
 struct TapeOp {
     int type = 0;
+    long pos[3] = {};  // OP_CCOND / OP_WFULL: element offsets e, p, q
     std::string spec;
     double alpha = 0.0, beta = 0.0;
     TV A, B, C;
@@ -289,6 +292,18 @@ dcsd_status apply_mterms(Ctx* c, int ref, bool fp32);
 // fixed-reference methods: zero the non-amplitude positions and the fixed
 // A->B element of the residual; set the fixed amplitude in c->t2
 dcsd_status apply_fr_mask(Ctx* c, int ref);
+// offsets in the union layout of the two internal singles (t alpha -> u
+// alpha, u beta -> t beta in frame A; their flips in frame B) in t1 / R1,
+// and of the A->B doubles element in t2 / R2
+struct InternalPos {
+    long s1, s2, e;
+};
+inline InternalPos internal_pos(const Ctx* c, int ref);
+// C-condition t2[A->B] = -t1[s1] t1[s2] (intermediate normalisation of the
+// two-determinant wave operator; zero in the CAS case)
+dcsd_status apply_c_condition(Ctx* c, int ref);
+// W = R2[A->B] + t1[s1] R1[s2] + t1[s2] R1[s1] into scal[0]
+dcsd_status coupling_w(Ctx* c, int ref);
 dcsd_status set_fixed_amplitude(Ctx* c, int ref, double value);
 // method codes (dcsd_method): DC modification, fixed-reference flag, fixed value
 inline bool method_valid(int m) { return m >= DCSD_CCSD && m <= DCSD_FR_DCSD_T; }
@@ -412,6 +427,15 @@ inline Frame frame_of(const Ctx* c, int ref) {
         f.occ_act[0] = u; f.occ_act[1] = t; f.vir_act[0] = 0; f.vir_act[1] = 1;
     }
     return f;
+}
+inline InternalPos internal_pos(const Ctx* c, int ref) {
+    const Frame f = frame_of(c, ref);
+    const long O = c->O, V = c->V;
+    InternalPos p;
+    p.s1 = (0 * O + f.occ_act[0]) * V + f.vir_act[0];
+    p.s2 = (1 * O + f.occ_act[1]) * V + f.vir_act[1];
+    p.e = (((2 * O + f.occ_act[0]) * O + f.occ_act[1]) * V + f.vir_act[0]) * V + f.vir_act[1];
+    return p;
 }
 
 }  // namespace dcsd

@@ -122,6 +122,44 @@ dcsd_status merge_r2f(Ctx* c) {
     return launch_check(c, "merge_r2f");
 }
 
+__global__ void k_c_condition(double* t2e, const double* t1s1, const double* t1s2) { *t2e = -(*t1s1) * (*t1s2); }
+
+dcsd_status apply_c_condition(Ctx* c, int ref) {
+    const InternalPos p = internal_pos(c, ref);
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_CCOND;
+        op.pos[0] = p.e;
+        op.pos[1] = p.s1;
+        op.pos[2] = p.s2;
+        rec_push(c, std::move(op));
+    }
+    k_c_condition<<<1, 1, 0, c->stream>>>(c->t2 + p.e, c->t1 + p.s1, c->t1 + p.s2);
+    return launch_check(c, "c_condition");
+}
+
+// W and the two singles residuals it used (kept for the reverse mode)
+__global__ void k_coupling_w(double* scal, const double* R2e, const double* t1, const double* R1, long s1, long s2) {
+    const double r1 = R1[s1], r2 = R1[s2];
+    scal[0] = *R2e + t1[s1] * r2 + t1[s2] * r1;
+    scal[50] = r1;
+    scal[51] = r2;
+}
+
+dcsd_status coupling_w(Ctx* c, int ref) {
+    const InternalPos p = internal_pos(c, ref);
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_WFULL;
+        op.pos[0] = p.e;
+        op.pos[1] = p.s1;
+        op.pos[2] = p.s2;
+        rec_push(c, std::move(op));
+    }
+    k_coupling_w<<<1, 1, 0, c->stream>>>(c->scal, c->R2 + p.e, c->t1, c->R1, p.s1, p.s2);
+    return launch_check(c, "coupling_w");
+}
+
 dcsd_status set_vvvv(Ctx* c, const double* host_vvvv) {
     const size_t V = c->V, nv4 = V * V * V * V;
     if (!c->vvvv && cudaMalloc((void**)&c->vvvv, nv4 * sizeof(double)) != cudaSuccess) {
@@ -175,8 +213,10 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         return einsum64(c, spec, alpha, A, Bm, beta, C);
     };
 
-    // fixed-reference methods: the A->B amplitude takes its fixed value
+    // the A->B amplitude: its fixed value (fixed-reference methods), or the
+    // C-condition (2D methods; zero in the CAS case)
     if (method_fr(method)) DCSD_TRY(set_fixed_amplitude(c, ref, method_fr_value(method)));
+    else DCSD_TRY(apply_c_condition(c, ref));
 
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
@@ -440,10 +480,14 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
         DCSD_TRY(merge_r2f(c));
     }
 
-    // ---- W = R^X at the A->B double; two-determinant terms ------------------------
-    {
-        long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
+    // ---- W = <B|H_N exp(T_A)|A>: R^X at the A->B double plus the products of
+    // the internal singles with their residuals (zero in the CAS case);
+    // two-determinant terms -------------------------------------------------------
+    if (method_fr(method)) {
+        const long e = (((2 * O + fr.occ_act[0]) * O + fr.occ_act[1]) * V + fr.vir_act[0]) * V + fr.vir_act[1];
         DCSD_TRY(copy_dev(c, c->scal, c->R2 + e, 1));
+    } else {
+        DCSD_TRY(coupling_w(c, ref));
     }
     // fixed-reference methods have no coupling terms (the element just read
     // is then the single-reference residual of the fixed excitation)

@@ -1044,6 +1044,12 @@ dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A, const
     return st;
 }
 
+// accuracy split of long BF16X6 contractions (at least 4 x 64 k-blocks):
+// FP32 partials over <= 64 k-blocks (4096 products), when the partial tiles
+// take at most 3 GB
+constexpr long kAccBlocks = 64;
+constexpr double kAccWorkspaceBytes = 3e9;
+
 dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, const TV& B, double beta,
                            const TV& C, int nsplit) {
     GemmPlan p;
@@ -1072,6 +1078,15 @@ dcsd_status einsum_tc_impl(Ctx* c, const char* spec, double alpha, const TV& A, 
         const long tilesMN = ((p.M + TC_BM - 1) / TC_BM) * ((p.N + bn - 1) / bn);
         if (tilesMN <= c->num_sms / 2 && nkt >= 64)
             ksplit = (int)std::max<long>(1, std::min<long>(c->num_sms / tilesMN, nkt / 16));
+        // BF16X6, the refinement precision: FP32 partial sums over at most
+        // kAccBlocks k-blocks, summed in FP64, when the partials fit (the
+        // rounding error of an FP32 sum grows with its length, and the long
+        // small-output contractions would otherwise dominate its error)
+        if (nsplit >= 3) {
+            const long need = (nkt + kAccBlocks - 1) / kAccBlocks;
+            if (need >= 4 && need > ksplit && (double)need * (double)p.M * (double)p.N * 4.0 <= kAccWorkspaceBytes)
+                ksplit = (int)need;
+        }
         const long kper = (nkt + ksplit - 1) / ksplit;
         const long waves = (tilesMN * ksplit + c->num_sms - 1) / std::max(1, c->num_sms);
         const double tc_us = (double)waves * (double)kper * 0.4 + (double)(p.M + p.N) * (double)p.K * 8.0 / 3e6;

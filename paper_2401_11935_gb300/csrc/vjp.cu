@@ -359,6 +359,29 @@ static bool ladder_reverse_pairs(Ctx* c, const TapeOp& op, const TV& R2b, bool w
     return true;
 }
 
+__global__ void k_ccond_adj(const double* t1, double* t1b, double* t2be, long p, long q) {
+    const double g = *t2be;
+    t1b[p] -= t1[q] * g;
+    t1b[q] -= t1[p] * g;
+    *t2be = 0.0;
+}
+
+__global__ void k_wfull_adj(const double* scal, double* sb, const double* t1, double* t1b, double* R1b, double* R2be,
+                            long p, long q) {
+    const double g = sb[0];
+    const double r1p = scal[50], r1q = scal[51];
+    if (R2be) *R2be += g;
+    if (t1b) {
+        t1b[p] += g * r1q;
+        t1b[q] += g * r1p;
+    }
+    if (R1b) {
+        R1b[q] += g * t1[p];
+        R1b[p] += g * t1[q];
+    }
+    sb[0] = 0.0;
+}
+
 dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
     TV Ab, Bb, Cb;
     switch (op.type) {
@@ -436,6 +459,25 @@ dcsd_status reverse_op(Ctx* c, const TapeOp& op) {
             DCSD_CUDA(c, cudaMemcpyAsync(sb, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
             DCSD_CUDA(c, cudaStreamSynchronize(c->stream));
             return DCSD_OK;
+        }
+        case OP_CCOND: {
+            // t2[e] = -t1[p] t1[q]: t1b[p] -= t1[q] t2b[e], t1b[q] -= t1[p] t2b[e], t2b[e] = 0
+            double* t1b = adj_of(c, c->t1);
+            double* t2b = adj_of(c, c->t2);
+            if (!t1b || !t2b) return DCSD_OK;
+            k_ccond_adj<<<1, 1, 0, c->stream>>>(c->t1, t1b, t2b + op.pos[0], op.pos[1], op.pos[2]);
+            return launch_check(c, "ccond_adj");
+        }
+        case OP_WFULL: {
+            // W = R2[e] + t1[p] R1[q] + t1[q] R1[p] with R1[p], R1[q] saved in scal[50..51]
+            double* sb = adj_of(c, c->scal);
+            double* t1b = adj_of(c, c->t1);
+            double* R1b = adj_of(c, c->R1);
+            double* R2b = adj_of(c, c->R2);
+            if (!sb) return DCSD_OK;
+            k_wfull_adj<<<1, 1, 0, c->stream>>>(c->scal, sb, c->t1, t1b, R1b, R2b ? R2b + op.pos[0] : nullptr,
+                                                 op.pos[1], op.pos[2]);
+            return launch_check(c, "wfull_adj");
         }
         case OP_SWAPVIR:
             return swap_vir_adjoint(c, adj_of(c, c->t2s), adj_of(c, c->t2));

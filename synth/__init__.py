@@ -16,7 +16,8 @@ Recipe (stand-in for the paper's molecules, which are not available):
     external virtuals ~ U[0.2,3.0] (sorted);
   * a Z2 "symmetry" label per orbital (t even, u odd, others random) and per
     auxiliary function, so t and u lie in different irreps (the CAS case of
-    Section II) and active-active singles vanish exactly;
+    Section II) and active-active singles vanish exactly; with ias=True t
+    and u are both even (the IAS case: the internal singles do not vanish);
   * DF factors B[L,p,q] ~ N(0, sigma^2), drawn for p<=q and mirrored, zeroed
     unless parity(p) xor parity(q) == parity(L).  sigma = 0.05 for the
     smallest workload (naux = 60, 21 virtuals per spin) and
@@ -72,11 +73,11 @@ class System:
         return self.n_v + 1
 
 
-def _parities(rng, n_c, n_v, naux):
+def _parities(rng, n_c, n_v, naux, ias=False):
     par = np.empty(n_c + 2 + n_v, dtype=np.int8)
     par[:n_c] = rng.integers(0, 2, n_c)
     par[n_c] = 0
-    par[n_c + 1] = 1
+    par[n_c + 1] = 0 if ias else 1
     par[n_c + 2:] = rng.integers(0, 2, n_v)
     par_aux = rng.integers(0, 2, naux).astype(np.int8)
     return par, par_aux
@@ -108,9 +109,11 @@ def b_sigma_for(naux, v):
 
 
 def make_system(name_or_dims, seed=None, eps_t=None, eps_u=None,
-                fock_noise=0.005, b_sigma=None) -> System:
+                fock_noise=0.005, b_sigma=None, ias=False) -> System:
     """Synthetic DF Hamiltonian for a named workload ('c1'..'c5') or for
-    explicit (n_c, n_v, naux)."""
+    explicit (n_c, n_v, naux).  ias=True gives t and u the same Z2 label
+    (the incomplete-active-space case of Section II: the internal singles
+    t -> u no longer vanish by symmetry)."""
     if isinstance(name_or_dims, str):
         n_c, n_v, naux, et, eu = CONFIGS[name_or_dims]
         if seed is None:
@@ -124,7 +127,7 @@ def make_system(name_or_dims, seed=None, eps_t=None, eps_u=None,
         eu = eps_u
     rng = np.random.Generator(np.random.PCG64(seed if seed is not None else 0))
     n = n_c + 2 + n_v
-    par, par_aux = _parities(rng, n_c, n_v, naux)
+    par, par_aux = _parities(rng, n_c, n_v, naux, ias)
     eps = np.empty(n)
     eps[:n_c] = np.sort(rng.uniform(-1.5, -0.3, n_c))
     eps[n_c] = et
@@ -138,14 +141,14 @@ def make_system(name_or_dims, seed=None, eps_t=None, eps_u=None,
 
 
 def make_pin_system(n_c, n_v, naux, seed, eps_t=-0.2, eps_u=-0.1,
-                    h_noise=0.02, b_sigma=0.15, z2=True) -> System:
+                    h_noise=0.02, b_sigma=0.15, z2=True, ias=False) -> System:
     """Small system defined by a spin-free core Hamiltonian h and DF factors
     B (for brute-force / FCI pins).  fock_a/fock_b are left as None-like
     zeros: the Fock matrices are built from h by the code under test."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = n_c + 2 + n_v
     if z2:
-        par, par_aux = _parities(rng, n_c, n_v, naux)
+        par, par_aux = _parities(rng, n_c, n_v, naux, ias)
     else:
         par = np.zeros(n, dtype=np.int8)
         par_aux = np.zeros(naux, dtype=np.int8)

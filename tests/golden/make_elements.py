@@ -21,6 +21,7 @@ element-wise oracle).  Checksums of the generated inputs let a consumer
 detect inputs that differ from these (another numpy random stream).
 
 Usage: python tests/golden/make_elements.py c5 [n_random_per_block]
+       python tests/golden/make_elements.py c5 --vjp-only   (recompute the derivative only)
 """
 import json
 import os
@@ -114,6 +115,32 @@ def positions(s, n_random, rng, edge=7):
     return out
 
 
+def vjp_entry(s, T, q_index):
+    """Derivative of the R2ab element q along the seeded direction d (the
+    C-condition fixes the A->B element, so d's component there does not
+    enter)."""
+    d = direction(T)
+
+    def r(e):
+        Te = tuple(t + e * x for t, x in zip(T, d))
+        return element.residual_element(element.ElementOracle(s, REF, METHOD, Te), 4, tuple(q_index))
+    deriv = (8.0 * (r(H) - r(-H)) - (r(2 * H) - r(-2 * H))) / (12.0 * H)
+    return {"block": 4, "index": list(q_index), "direction_seed": DIR_SEED, "h": H, "value": deriv}, d
+
+
+def vjp_only(name):
+    """Recompute only the stored reverse-mode derivative of an existing file."""
+    path = os.path.join(HERE, f"{name}_elements.json")
+    res = json.load(open(path))
+    s = make_system(name)
+    T = random_amplitudes(s, seed=SEED, ref=REF, scale1=SCALE, scale2=SCALE)
+    res["vjp"], d = vjp_entry(s, T, res["vjp"]["index"])
+    res["checksums"] = checksums(s, T, d)
+    print("vjp directional derivative", res["vjp"]["value"], flush=True)
+    with open(path, "w") as f:
+        json.dump(res, f, indent=1)
+
+
 def main(name, n):
     t0 = time.time()
     s = make_system(name)
@@ -132,14 +159,8 @@ def main(name, n):
         print(blk, idx, kind, val, rec.get("ladder"), flush=True)
     # reverse mode: d/de R_q(T + e d) for the first sampled R2ab element
     q = next(e for e in res["elements"] if e["block"] == 4)
-    d = direction(T)
-
-    def r(e):
-        Te = tuple(t + e * x for t, x in zip(T, d))
-        return element.residual_element(element.ElementOracle(s, REF, METHOD, Te), 4, tuple(q["index"]))
-    deriv = (8.0 * (r(H) - r(-H)) - (r(2 * H) - r(-2 * H))) / (12.0 * H)
-    res["vjp"] = {"block": 4, "index": q["index"], "direction_seed": DIR_SEED, "h": H, "value": deriv}
-    print("vjp directional derivative", deriv, flush=True)
+    res["vjp"], d = vjp_entry(s, T, q["index"])
+    print("vjp directional derivative", res["vjp"]["value"], flush=True)
     res["checksums"] = checksums(s, T, d)
     res["oracle_seconds"] = time.time() - t0
     with open(os.path.join(HERE, f"{name}_elements.json"), "w") as f:
@@ -147,4 +168,7 @@ def main(name, n):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "c5", int(sys.argv[2]) if len(sys.argv) > 2 else 4)
+    if "--vjp-only" in sys.argv:
+        vjp_only(sys.argv[1])
+    else:
+        main(sys.argv[1] if len(sys.argv) > 1 else "c5", int(sys.argv[2]) if len(sys.argv) > 2 else 4)

@@ -1,7 +1,7 @@
 """Write oracle energies of the named workloads to tests/golden/*.json.
 
 Calls only the CPU oracle (oracle/) and the seeded generator (synth/).
-Usage: python tests/golden/make_golden.py c1 [c2 ...]
+Usage: python tests/golden/make_golden.py c1 [c2 ...] [--only 2D-DCSD]
 The GPU tests compare the library's converged energies with these files:
 2D-CCSD and 2D-DCSD (Section II), and the fixed-reference FR-CCSD and
 FR-DCSD (Section I) for the singlet (fixed amplitude +1) and the M_s = 0
@@ -52,12 +52,16 @@ def response(s, method, tol, h=0.05):
             "dE_S": d[0], "dE_T": d[1]}
 
 
-def main(names):
+def main(names, only=None):
+    """only: restrict to one entry of the results (e.g. "2D-DCSD") -- the
+    second workload's oracle solve takes hours per method."""
     for name in names:
         s = make_system(name)
         out = {"workload": name, "dims": CONFIGS[name][:3], "seed": CONFIG_SEED[name],
                "b_sigma": b_sigma_for(s.naux, s.v), "generator": "synth.make_system", "results": {}}
         for method, mname in ((0, "2D-CCSD"), (1, "2D-DCSD")):
+            if only and mname != only:
+                continue
             t0 = time.time()
             _, info = solve.solve(s, method, ref=0, tol=TOL[name], maxiter=300, verbose=True)
             out["results"][mname] = {k: float(info[k]) for k in ("dEA", "W", "E_S", "E_T", "max_r")}
@@ -67,6 +71,8 @@ def main(names):
             print(name, mname, out["results"][mname], flush=True)
         for method, mname in ((0, "FR-CCSD"), (1, "FR-DCSD")):
             for sign, st in ((1.0, "S"), (-1.0, "T")):
+                if only and f"{mname} {st}" != only:
+                    continue
                 t0 = time.time()
                 _, info = solve.solve(s, method, ref=0, tol=TOL[name], maxiter=300, fixed=sign)
                 key = f"{mname} {st}"
@@ -85,4 +91,10 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["c1"])
+    args = sys.argv[1:]
+    only = None
+    if "--only" in args:
+        k = args.index("--only")
+        only = args[k + 1]
+        del args[k:k + 2]
+    main(args or ["c1"], only)

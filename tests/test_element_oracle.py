@@ -38,7 +38,7 @@ def test_amplitude_slices_match_dense_tensor():
     s = make_system((2, 3, 10), seed=7)
     T = random_amplitudes(s, seed=8, ref=0, scale1=0.1, scale2=0.1, z2=False)
     eo = element.ElementOracle(s, 0, 1, T)
-    _, t2 = unpack(eo.o, eo.v, T)
+    _, t2 = unpack(eo.o, eo.v, twod.c_condition(T))
     rng = np.random.default_rng(1)
     for mask in np.ndindex(2, 2, 2, 2):
         for _ in range(4):

@@ -52,7 +52,8 @@ def test_p3_ccsd_residual_vs_ci_vectors(nc, nv, X, z2, ref):
 @pytest.mark.parametrize("ref", [0, 1])
 def test_p2_twod_residual_vs_bloch_form(nc, nv, X, z2, ref):
     s, _ = _pin(nc, nv, X, z2)
-    T = random_amplitudes(s, seed=4, z2=z2, scale1=0.05, scale2=0.05)
+    # the C-condition fixes the A->B element (non-zero for non-CAS amplitudes)
+    T = twod.c_condition(random_amplitudes(s, seed=4, z2=z2, scale1=0.05, scale2=0.05))
     fr, fro = twod.frames(s, ref)
     t1, t2 = unpack(fr.o, fr.v, T)
     t1o, t2o = unpack(fr.o, fr.v, flip_abi(T))

@@ -18,8 +18,11 @@ from oracle.spinorb import unpack
 
 
 def _antisym_dir(rng, T):
+    # the A->B element is not a free amplitude (the C-condition fixes it)
     d = [rng.normal(0, 1, t.shape) for t in T]
     d[2], d[3] = ovjp.antisym(d[2]), ovjp.antisym(d[3])
+    o = d[0].shape[0]
+    d[4][o - 1, o - 1, 0, 0] = 0.0
     return d
 
 

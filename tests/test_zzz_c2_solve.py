@@ -36,7 +36,7 @@ def check_against_element_oracle(s, method, T, dEA, W, tol_e=1e-10, tol_r=1e-9, 
     assert abs(eo.energy() - dEA) < tol_e
     assert abs(eo.W() - W) < tol_e
     worst = 0.0
-    for blk, idx in _positions()(s, per_block, np.random.default_rng(5)):
+    for blk, idx, _ in _positions()(s, per_block, np.random.default_rng(5)):
         worst = max(worst, abs(element.residual_element(eo, blk, idx)))
     assert worst < tol_r, worst
     return worst
