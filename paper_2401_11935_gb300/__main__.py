@@ -7,6 +7,8 @@ for profiler captures of single kernels).
     python -m paper_2401_11935_gb300 vjp --dims c4 --repeat 2
     python -m paper_2401_11935_gb300 vjp --dims c5 --precision bf16x6
     python -m paper_2401_11935_gb300 lambda --dims c4
+    python -m paper_2401_11935_gb300 stgap --fcidump SA --singlet S --triplet T
+    python -m paper_2401_11935_gb300 stgap --dims 4,20,60 --rotate 0.05
 
 compare converges the FP64 and the mixed-precision solves from the same
 guess and prints their energies (Delta E_A, W, singlet and triplet energies,
@@ -31,7 +33,13 @@ PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "mixed": 3, "bf16x6": 4}
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2401_11935_gb300")
-    ap.add_argument("what", choices=["residual", "solve", "compare", "vjp", "lambda"])
+    ap.add_argument("what", choices=["residual", "solve", "compare", "vjp", "lambda", "stgap"])
+    ap.add_argument("--fcidump", default=None, help="stgap: FCIDUMP of the single calculation")
+    ap.add_argument("--singlet", default=None, help="stgap: FCIDUMP of the singlet's own orbitals")
+    ap.add_argument("--triplet", default=None, help="stgap: FCIDUMP of the triplet's own orbitals")
+    ap.add_argument("--rotate", type=float, default=0.05,
+                    help="stgap without files: size of the orbital rotations of the synthetic sets")
+    ap.add_argument("--frozen", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--switch-tol", type=float, default=1e-5)
     ap.add_argument("--polish-tol", type=float, default=1e-7)
@@ -53,6 +61,8 @@ def main(argv=None):
     from synth import CONFIGS, make_system, random_amplitudes
     import paper_2401_11935_gb300 as P
 
+    if a.what == "stgap":
+        return stgap_main(a, P)
     if a.dims in CONFIGS:
         s = make_system(a.dims)
     else:
@@ -112,6 +122,46 @@ def main(argv=None):
                   f"{f.seconds / m.seconds:.2f}", flush=True)
     finally:
         eng.close()
+
+
+def stgap_main(a, P):
+    """Singlet-triplet gaps from one calculation (the first file) and from
+    two (singlet and triplet files).  Without files, three orbital sets of a
+    synthetic system (core Hamiltonian and four-index integrals) are written
+    to a temporary directory: the generated orbitals and two sets rotated by
+    occupied-virtual mixing of size --rotate."""
+    import tempfile
+    from paper_2401_11935_gb300 import stgap
+    method = P.DCSD if a.method == "dcsd" else P.CCSD
+    paths = [a.fcidump, a.singlet, a.triplet]
+    tmp = None
+    if a.fcidump is None:
+        from synth import make_pin_system
+        from synth import fcidump as wf
+        dims = tuple(int(x) for x in a.dims.split(",")) if "," in a.dims else (4, 20, 60)
+        s = make_pin_system(*dims, seed=a.seed, b_sigma=0.08)
+        eri = wf.eri_from_factors(s.B)
+        tmp = tempfile.TemporaryDirectory()
+        sets = [(s.h, eri)] + [wf.rotate(s.h, eri, wf.random_ov_rotation(s.parity, s.n_c + 2, a.rotate, a.seed + k))
+                               for k in (1, 2)]
+        paths = []
+        for k, (h, e) in enumerate(sets):
+            p = os.path.join(tmp.name, f"FCIDUMP.{k}")
+            wf.write(p, h, e, 2 * s.n_c + 2, 0, orbsym=[1 + int(x) for x in s.parity])
+            paths.append(p)
+    g = stgap.gaps(paths[0], singlet=paths[1], triplet=paths[2], method=method, n_frozen=a.frozen, tol=a.tol,
+                   precision=PREC[a.precision or "fp64"], maxiter=a.maxiter)
+    one = g["single"]
+    print(f"one calculation:  E_S {one['E_S']:.10f}  E_T {one['E_T']:.10f}  gap {one['gap']:.10f} Eh "
+          f"({one['gap'] * 27.211386:.4f} eV)  {one['iters']} iterations, {one['seconds']:.3f} s", flush=True)
+    if "state_specific" in g:
+        ss = g["state_specific"]
+        print(f"two calculations: E_S {ss['E_S']:.10f}  E_T {ss['E_T']:.10f}  gap {ss['gap']:.10f} Eh "
+              f"({ss['gap'] * 27.211386:.4f} eV)  {ss['iters']} iterations, {ss['seconds']:.3f} s", flush=True)
+        print(f"difference (one - two): {(one['gap'] - ss['gap']) * 27211.386:+.3f} meV", flush=True)
+    if tmp is not None:
+        tmp.cleanup()
+    return 0
 
 
 if __name__ == "__main__":

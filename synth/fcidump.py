@@ -40,3 +40,34 @@ def eri_from_factors(B):
     """(pq|rs) = sum_L B[L,p,q] B[L,r,s] -- the four-index array a DF
     factor set stands for (layout conversion of the synthetic inputs)."""
     return np.einsum("Lpq,Lrs->pqrs", B, B, optimize=True)
+
+
+def random_ov_rotation(parity, n_occ, scale, seed):
+    """A seeded orthogonal orbital rotation U = exp(K) that mixes the first
+    n_occ orbitals (occupied in the reference) with the rest, only within
+    the same symmetry label: K antisymmetric, K[p, q] ~ N(0, scale^2) for p
+    occupied, q virtual, parity[p] == parity[q].  Stands in for the orbital
+    relaxation between two orbital sets of one molecule (state-averaged vs
+    state-specific orbitals)."""
+    from scipy.linalg import expm
+    n = len(parity)
+    rng = np.random.default_rng(seed)
+    K = np.zeros((n, n))
+    for p in range(n_occ):
+        for q in range(n_occ, n):
+            if parity[p] == parity[q]:
+                K[p, q] = rng.normal(0.0, scale)
+    K = K - K.T
+    return expm(K)
+
+
+def rotate(h, eri, U):
+    """Integrals in the rotated orbitals phi'_p = sum_q phi_q U[q, p]:
+    h' = U^T h U, (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd) (a basis change
+    of the inputs)."""
+    h2 = U.T @ h @ U
+    e = np.einsum("abcd,ap->pbcd", eri, U, optimize=True)
+    e = np.einsum("pbcd,bq->pqcd", e, U, optimize=True)
+    e = np.einsum("pqcd,cr->pqrd", e, U, optimize=True)
+    e = np.einsum("pqrd,ds->pqrs", e, U, optimize=True)
+    return h2, e
