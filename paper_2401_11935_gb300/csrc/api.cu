@@ -325,6 +325,8 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
         c->trace_seq = tr && tr[0] == '2';
         const char* vb = getenv("DCSD_VERBOSE");
         c->verbose = vb && vb[0] == '1';
+        const char* mc = getenv("DCSD_TC_MULTICAST");
+        c->tc_multicast = !(mc && mc[0] == '0');
     }
     c->nc = d->n_c;
     c->nv = d->n_v;

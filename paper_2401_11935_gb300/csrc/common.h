@@ -161,6 +161,9 @@ struct Ctx {
     const double* pack_cache_src[2] = {};
     double* hostbuf = nullptr;    // pinned host staging for scalars
     int ladder_chunk = 8;         // virtual rows per V build chunk (FP64)
+    // the ladder contraction in clusters of two CTAs sharing each B tile by
+    // TMA multicast (DCSD_TC_MULTICAST=0 selects the one-CTA kernel)
+    bool tc_multicast = true;
 
     MTables* mt[2] = {};          // per reference
     TcEngine* tc = nullptr;

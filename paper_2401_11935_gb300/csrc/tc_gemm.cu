@@ -84,6 +84,25 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
+// the same load delivered to the same shared-memory offset of every CTA in
+// ctaMask (this GPU's own memory; cluster of two CTAs), completing bytes on
+// the mbarrier at the same offset in each
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -108,6 +127,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+// completion of the issued MMAs signalled on the mbarrier at the same offset
+// in every CTA of ctaMask
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile(
@@ -249,7 +277,14 @@ __device__ __forceinline__ void tile_mn(int mn, int tilesM, int tilesN, int grou
 
 // two TMEM accumulators of BN columns let the epilogue of one tile overlap
 // the MMAs of the next.
-template <int BN>
+//
+// MC: launched in clusters of two CTAs that take the two m-tiles of a pair
+// with the same n-tile.  Each CTA loads its own A tile and half of the B tile
+// (BN / 2 rows; tmB's box is that half) and multicasts the half to both, so
+// the pair fetches each B tile from L2 once.  A stage slot is free only when
+// both CTAs' MMAs have consumed it: the MMA completion is signalled on the
+// empty barrier of both CTAs (count 2), and every TMA issue waits for it.
+template <int BN, bool MC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcEpi epi,
               int nkt, int tilesM, int tilesN, int kper, int group, int kblk, int* err) {
@@ -268,13 +303,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // tiles enumerate (m tile, n tile, k split); split s covers the k-steps
-    // [s * kper, min(nkt, (s + 1) * kper))
-    const int nmn = tilesM * tilesN;
+    // [s * kper, min(nkt, (s + 1) * kper)).  MC: the schedule runs over pairs
+    // of m-tiles (the pair's CTA of rank r takes m-tile 2 * pair + r; an
+    // m-tile beyond the last one reads zeros and stores nothing)
+    const int crank = MC ? (int)cluster_rank() : 0;
+    const int tile0 = MC ? (int)blockIdx.x / 2 : (int)blockIdx.x;
+    const int tstep = MC ? (int)gridDim.x / 2 : (int)gridDim.x;
+    const int tilesMs = MC ? (tilesM + 1) / 2 : tilesM;
+    const int nmn = tilesMs * tilesN;
     const int ntiles = nmn * ((nkt + kper - 1) / kper);
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MC ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -289,16 +330,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // MC: the peer's barriers are initialised before any multicast reaches them
+    if (MC) cluster_sync();
     const uint32_t tmem = *tslot;
 
     if (warp == 0) {
         if (lane == 0) {
             int g = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int tile = tile0; tile < ntiles && ok; tile += tstep) {
                 const int mn = tile % nmn, ks = tile / nmn;
                 int tm, tn;
-                tile_mn(mn, tilesM, tilesN, group, tm, tn);
+                tile_mn(mn, tilesMs, tilesN, group, tm, tn);
+                if (MC) tm = 2 * tm + crank;
                 const int m0 = tm * TC_BM, n0 = tn * BN;
                 const int kb = ks * kper, ke = min(nkt, kb + kper);
                 for (int kt = kb; kt < ke; ++kt, ++g) {
@@ -309,7 +353,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     mbar_expect_tx(&full[s], STAGE);
-                    if (kblk) {
+                    if (MC) {
+                        tma_load_3d(smem + s * STAGE, &tmA, &full[s], 0, m0, kt);
+                        tma_load_3d_mc(smem + s * STAGE + A_BYTES + crank * (B_BYTES / 2), &tmB, &full[s], 0,
+                                       n0 + crank * (BN / 2), kt, (uint16_t)0x3);
+                    } else if (kblk) {
                         tma_load_3d(smem + s * STAGE, &tmA, &full[s], 0, m0, kt);
                         tma_load_3d(smem + s * STAGE + A_BYTES, &tmB, &full[s], 0, n0, kt);
                     } else {
@@ -319,6 +367,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     *issued = g + 1;
                 }
             }
+            if (MC) {
+                // every slot free in both CTAs: the peer's last MMA completions
+                // have arrived here and no multicast of this CTA is pending
+                const int g0 = max(0, g - TC_STAGES);
+                for (int gg = g0; gg < g; ++gg)
+                    if (!mbar_wait(&empty[gg % TC_STAGES], (gg / TC_STAGES) & 1)) atomicExch(err, 5);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -326,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                        ((uint32_t)(TC_BM >> 4) << 24);
             int g = 0, j = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
+            for (int tile = tile0; tile < ntiles && ok; tile += tstep, ++j) {
                 const int buf = j & 1, u = j >> 1;
                 if (u > 0 && !mbar_wait(&acce[buf], (u - 1) & 1)) {
                     atomicExch(err, 4);
@@ -349,7 +404,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int kk = 0; kk < TC_BK / 16; ++kk)
                         mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
                                  (kt > kb || kk > 0) ? 1u : 0u);
-                    mma_commit(&empty[s]);
+                    if (MC) mma_commit_mc(&empty[s], (uint16_t)0x3);
+                    else mma_commit(&empty[s]);
                     *consumed = g + 1;
                 }
                 if (ok) mma_commit(&accf[buf]);
@@ -367,11 +423,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int q = warp & 3;
         const int ch0 = ((warp - 2) >> 2) * (BN / 64), ch1 = ch0 + BN / 64;
         int j = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+        for (int tile = tile0; tile < ntiles; tile += tstep, ++j) {
             const int buf = j & 1, u = j >> 1;
             const int mn = tile % nmn, ksp = tile / nmn;
             int tm, tn;
-            tile_mn(mn, tilesM, tilesN, group, tm, tn);
+            tile_mn(mn, tilesMs, tilesN, group, tm, tn);
+            if (MC) tm = 2 * tm + crank;
             const int m0 = tm * TC_BM, n0 = tn * BN;
             const bool ok = mbar_wait(&accf[buf], u & 1);
             tc_fence_after();
@@ -544,6 +601,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    __syncwarp();
+    if (MC) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -674,6 +733,7 @@ struct Buf {
 struct TcEngine {
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     int* d_err = nullptr;
+    int mc_clusters[2] = {0, 0};  // resident two-CTA clusters (BN 128, 256); 0 unknown, -1 none
     Buf pa, pb, pv, pt;  // generic A, generic B, ladder V tile, stacked amplitudes
     bool attr_set = false;
     // ladder row tables for the stacked amplitudes [aa pairs; bb pairs; ab; ab~]
@@ -857,17 +917,54 @@ static dcsd_status make_map_kblk(Ctx* c, CUtensorMap* map, const __nv_bfloat16* 
 // C (epilogue epi) = A[M][Ktot] . B[N][Ktot]^T; the operands are K-major BF16
 // with row pitch `pitch` elements (0: Ktot), or K-blocked (kblocked: both
 // operands [Ktot / 64][rows][64])
+// mc (K-blocked operands, at least two m-tiles): clusters of two CTAs share
+// each B tile through TMA multicast (see k_tc_gemm)
 static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __nv_bfloat16* Bp, long N,
-                               long Ktot, TcEpi& epi, int ksplit = 1, long pitch = 0, bool kblocked = false) {
+                               long Ktot, TcEpi& epi, int ksplit = 1, long pitch = 0, bool kblocked = false,
+                               bool mc = false) {
     TcEngine* e = c->tc;
     if (!e->attr_set) {
         size_t s256 = TC_STAGES * (TC_BM * TC_BK * 2 + 256 * TC_BK * 2) + kStageBytesMode2 + 2048;
         size_t s128 = TC_STAGES * (TC_BM * TC_BK * 2 + 128 * TC_BK * 2) + kStageBytesMode2 + 2048;
-        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s256));
-        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s128));
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)s256));
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)s128));
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)s256));
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)s128));
         e->attr_set = true;
     }
     const int BN = N >= 256 ? 256 : 128;
+    mc = mc && kblocked && c->tc_multicast && M > TC_BM && c->num_sms >= 2;
+    long max_clusters = c->num_sms / 2;
+    if (mc) {
+        if (e->mc_clusters[BN == 256 ? 1 : 0] == 0) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3((unsigned)(2 * max_clusters));
+            q.blockDim = dim3(kTcThreads);
+            q.dynamicSmemBytes = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            q.attrs = at;
+            q.numAttrs = 1;
+            int nclu = 0;
+            const cudaError_t qe = BN == 256 ? cudaOccupancyMaxActiveClusters(&nclu, k_tc_gemm<256, true>, &q)
+                                             : cudaOccupancyMaxActiveClusters(&nclu, k_tc_gemm<128, true>, &q);
+            if (qe != cudaSuccess || nclu < 1) {
+                cudaGetLastError();
+                nclu = -1;  // clusters unavailable: the one-CTA kernel runs
+            }
+            e->mc_clusters[BN == 256 ? 1 : 0] = nclu;
+        }
+        const int nclu = e->mc_clusters[BN == 256 ? 1 : 0];
+        if (nclu < 1) mc = false;
+        else max_clusters = std::min<long>(max_clusters, nclu);
+    }
     CUtensorMap ma, mb;
     if (pitch != 0 && (pitch < Ktot || pitch % 8 != 0 || ((uintptr_t)Ap | (uintptr_t)Bp) % 16 != 0)) {
         c->err = "tensor-core GEMM: operand pitch or base not aligned";
@@ -879,7 +976,7 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
             return DCSD_ERR_INVALID_ARG;
         }
         DCSD_TRY(make_map_kblk(c, &ma, Ap, M, Ktot, TC_BM));
-        DCSD_TRY(make_map_kblk(c, &mb, Bp, N, Ktot, BN));
+        DCSD_TRY(make_map_kblk(c, &mb, Bp, N, Ktot, mc ? BN / 2 : BN));
     } else {
         DCSD_TRY(make_map(c, &ma, Ap, M, Ktot, TC_BM, pitch));
         DCSD_TRY(make_map(c, &mb, Bp, N, Ktot, BN, pitch));
@@ -899,7 +996,11 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
         c->err = "tensor-core GEMM too large";
         return DCSD_ERR_INVALID_ARG;
     }
-    dim3 grid((unsigned)std::min<long>(ntiles, c->num_sms));
+    // MC: the schedule runs over pairs of m-tiles, two CTAs per pair; as many
+    // clusters as can be resident at once (a persistent grid)
+    const long tilesMs = mc ? (tilesM + 1) / 2 : tilesM;
+    const long ntiles_s = tilesMs * tilesN * ((nkt + kper - 1) / kper);
+    dim3 grid((unsigned)(mc ? 2 * std::min<long>(ntiles_s, max_clusters) : std::min<long>(ntiles, c->num_sms)));
     // m-tile band height that minimises the A and B rows one wave of
     // num_sms tiles touches: g * BM + (num_sms / g) * BN
     // (an operand that fits in a quarter of L2 is kept there instead: all
@@ -910,6 +1011,7 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
     if ((double)M * (double)Ktot * 2.0 <= l2q || c->ladder_phase) group = (int)tilesM;
     else if ((double)N * (double)Ktot * 2.0 <= l2q) group = 1;
     group = (int)std::max<long>(1, std::min<long>(group, tilesM));
+    if (mc) group = (int)std::max<long>(1, std::min<long>((group + 1) / 2, tilesMs));
     size_t smem = TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + kStageBytesMode2 + 2048;
     const int cls = c->ladder_phase ? DCSD_PROF_LADDER : DCSD_PROF_TC_OTHER;
     prof_begin(c, cls);
@@ -921,12 +1023,38 @@ static dcsd_status gemm_packed(Ctx* c, const __nv_bfloat16* Ap, long M, const __
         trace_begin(c, label);
     }
     ++c->tc_seq;
-    if (BN == 256)
-        k_tc_gemm<256><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group,
-                                                              kblocked ? 1 : 0, e->d_err);
-    else
-        k_tc_gemm<128><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper, group,
-                                                              kblocked ? 1 : 0, e->d_err);
+    if (mc) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const int tm = (int)tilesM, tn = (int)tilesN, kb = 1;
+        cudaError_t le = BN == 256 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<256, true>, ma, mb, epi, nkt, tm, tn, kper, group,
+                                                        kb, e->d_err)
+                                   : cudaLaunchKernelEx(&cfg, k_tc_gemm<128, true>, ma, mb, epi, nkt, tm, tn, kper, group,
+                                                        kb, e->d_err);
+        if (le != cudaSuccess) {
+            trace_end(c);
+            prof_end(c, cls);
+            c->err = std::string("tc_gemm (cluster launch): ") + cudaGetErrorString(le);
+            cudaGetLastError();
+            return DCSD_ERR_CUDA;
+        }
+    } else if (BN == 256) {
+        k_tc_gemm<256, false><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper,
+                                                                     group, kblocked ? 1 : 0, e->d_err);
+    } else {
+        k_tc_gemm<128, false><<<grid, kTcThreads, smem, c->stream>>>(ma, mb, epi, nkt, (int)tilesM, (int)tilesN, kper,
+                                                                     group, kblocked ? 1 : 0, e->d_err);
+    }
     trace_end(c);
     prof_end(c, cls);
     return launch_check(c, "tc_gemm");
@@ -1389,7 +1517,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 // (the scatter epilogue adds)
                 for (int sp = 0; sp < nseg; ++sp)
                     DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
-                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true));
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true, true));
             } else {
                 ce.C = G + r0 * V;       // G[s][i][j][k][b], row (s,i,j) at the table's offset
                 ce.mrow = e->d_growoff;
@@ -1399,7 +1527,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
                 for (int sp = 0; sp < nseg; ++sp) {
                     ce.beta = sp == 0 ? 0.0 : 1.0;
                     DCSD_TRY(gemm_packed(c, e->pt.p + (size_t)sp * rows4 * K2p, rows4,
-                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true));
+                                         e->pv.p + (size_t)sp * vrows * K2p, vrows, K2p, ce, 1, 0, true, true));
                 }
             }
         }
