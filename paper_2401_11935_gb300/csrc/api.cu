@@ -217,6 +217,10 @@ void free_ctx(Ctx* c) {
     c->vvvv = nullptr;
     if (c->r2f) cudaFree(c->r2f);
     c->r2f = nullptr;
+    if (c->t2img) cudaFree(c->t2img);
+    c->t2img = nullptr;
+    c->t2img_cap = 0;
+    c->t2img_src = nullptr;
     if (c->hostbuf) cudaFreeHost(c->hostbuf);
     c->hostbuf = nullptr;
     for (int k = 0; k < 8; ++k) {
@@ -327,6 +331,8 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
         c->verbose = vb && vb[0] == '1';
         const char* mc = getenv("DCSD_TC_MULTICAST");
         c->tc_multicast = !(mc && mc[0] == '0');
+        const char* pg = getenv("DCSD_PACK_GENERIC");
+        c->pack_generic = pg && pg[0] == '1';
     }
     c->nc = d->n_c;
     c->nv = d->n_v;

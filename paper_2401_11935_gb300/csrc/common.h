@@ -159,11 +159,23 @@ struct Ctx {
     // operands the tensor-core engine may keep packed between contractions
     // (pack_cache_set; valid only while their data does not change)
     const double* pack_cache_src[2] = {};
+    // BF16 image of t2 for the operand packs of one tensor-core residual:
+    // plane p holds part p of the split of every element (plane stride
+    // t2img_plane elements).  Valid while t2img_src is set: residual_union
+    // builds it after the last write to t2 and clears it on return.
+    uint16_t* t2img = nullptr;
+    size_t t2img_cap = 0;             // elements, all planes
+    const double* t2img_src = nullptr;
+    long t2img_len = 0, t2img_plane = 0;
+    int t2img_planes = 0;
     double* hostbuf = nullptr;    // pinned host staging for scalars
     int ladder_chunk = 8;         // virtual rows per V build chunk (FP64)
     // the ladder contraction in clusters of two CTAs sharing each B tile by
     // TMA multicast (DCSD_TC_MULTICAST=0 selects the one-CTA kernel)
     bool tc_multicast = true;
+    // operand packs: the tiled FP64 kernel only, without the t2 image and the
+    // row kernel (DCSD_PACK_GENERIC=1; both give identical operands)
+    bool pack_generic = false;
 
     MTables* mt[2] = {};          // per reference
     TcEngine* tc = nullptr;
@@ -272,6 +284,11 @@ dcsd_status dot_view(Ctx* c, const TV& A, const TV& B, double* out, double accum
 dcsd_status fill(Ctx* c, double* p, size_t n, double val);
 // C += sum_k alpha_k A_k over up to 4 rank-4 views (one pass)
 dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C);
+// R[i][j][a][b] += X[i][a][j][b] - X[j][a][i][b] - X[i][b][j][a] + X[j][b][i][a]
+// (X [O][V][O][V], R [O][O][V][V]); recorded as that four-view axpy4
+dcsd_status ring_antisym_add(Ctx* c, const TV& X, const TV& R);
+// R[i][j][a][b] += X[j][b][i][a]; recorded as that axpy_view
+dcsd_status add_swapped(Ctx* c, const TV& X, const TV& R);
 // out[k] = <x, ys[k]> for k < m <= 16, contiguous vectors of length n (device out)
 dcsd_status multidot(Ctx* c, const double* x, const double* const* ys_host, int m, long n, double* out);
 
@@ -373,6 +390,8 @@ dcsd_status einsum_tc(Ctx* c, const char* spec, double alpha, const TV& A,
 dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G);
 // sources whose packed operands einsum_tc may reuse (NULL: none); clears the cache
 void pack_cache_set(Ctx* c, const double* src0, const double* src1);
+// the BF16 image of t2 with the parts of an nsplit-way split (see Ctx)
+dcsd_status t2_image(Ctx* c, int nsplit);
 
 // record a CUDA event pair around a launch of class cls when profiling
 inline void prof_begin(Ctx* c, int cls) {

@@ -658,18 +658,20 @@ __global__ void __launch_bounds__(256) k_axpy4(Axpy4Args a) {
     }
 }
 
-dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C) {
-    if (c->rec) {
-        TapeOp op;
-        op.type = OP_AXPY4;
-        op.nv = std::min(nv, 4);
-        for (int k = 0; k < op.nv; ++k) {
-            op.X[k] = A[k];
-            op.al[k] = alpha[k];
-        }
-        op.C = C;
-        rec_push(c, std::move(op));
+static void record_axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C) {
+    TapeOp op;
+    op.type = OP_AXPY4;
+    op.nv = std::min(nv, 4);
+    for (int k = 0; k < op.nv; ++k) {
+        op.X[k] = A[k];
+        op.al[k] = alpha[k];
     }
+    op.C = C;
+    rec_push(c, std::move(op));
+}
+
+dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C) {
+    if (c->rec) record_axpy4(c, nv, alpha, A, C);
     Axpy4Args a;
     if (C.rank != 4 || nv < 1 || nv > 4) {
         c->err = "axpy4 needs rank-4 views";
@@ -694,6 +696,137 @@ dcsd_status axpy4(Ctx* c, int nv, const double* alpha, const TV* A, const TV& C)
     k_axpy4<<<(unsigned)std::max<long>(1, std::min<long>(nrow, (long)c->num_sms * 32)), 256, 0, c->stream>>>(a);
     trace_end(c);
     return launch_check(c, "axpy4");
+}
+
+// R[i][j][a][b] += X[i][a][j][b] - X[j][a][i][b] - X[i][b][j][a] + X[j][b][i][a]
+// for X [O][V][O][V] and R [O][O][V][V], both contiguous.  With
+// D_ij[a][b] = X[i][a][j][b] - X[j][a][i][b] the increment is
+// D_ij[a][b] - D_ij[b][a], and D_ji = -D_ij, so one work item (a pair i < j
+// and a pair of 32-wide (a, b) tiles A <= B) reads the four X tiles once and
+// updates R[i][j] and R[j][i] on both tiles; for i = j the increment is zero.
+__global__ void __launch_bounds__(256) k_ring_antisym(const double* __restrict__ X, double* __restrict__ R, int O,
+                                                      int V) {
+    __shared__ double dab[32][33], dba[32][33];
+    const int nt = (V + 31) / 32;
+    const long ntp = (long)nt * (nt + 1) / 2, npair = (long)O * (O - 1) / 2;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long OV = (long)O * V, VV = (long)V * V;
+    for (long w = blockIdx.x; w < npair * ntp; w += gridDim.x) {
+        long pr = w / ntp, tp = w - pr * ntp;
+        int i = 0;
+        while (pr >= O - 1 - i) {
+            pr -= O - 1 - i;
+            ++i;
+        }
+        const int j = i + 1 + (int)pr;
+        int ta = 0;
+        while (tp >= nt - ta) {
+            tp -= nt - ta;
+            ++ta;
+        }
+        const int tb = ta + (int)tp;
+        const int a0 = 32 * ta, b0 = 32 * tb;
+        const double* Xij = X + (long)i * V * OV + (long)j * V;  // X[i][a][j][b] at a * OV + b
+        const double* Xji = X + (long)j * V * OV + (long)i * V;
+        for (int r = ty; r < 32; r += 8) {
+            const long a = a0 + r, b = b0 + tx;            // dab[r][x] = D[a0 + r][b0 + x]
+            dab[r][tx] = (a < V && b < V) ? Xij[a * OV + b] - Xji[a * OV + b] : 0.0;
+            const long a2 = b0 + r, b2 = a0 + tx;          // dba[r][x] = D[b0 + r][a0 + x]
+            dba[r][tx] = (a2 < V && b2 < V) ? Xij[a2 * OV + b2] - Xji[a2 * OV + b2] : 0.0;
+        }
+        __syncthreads();
+        double* Rij = R + ((long)i * O + j) * VV;
+        double* Rji = R + ((long)j * O + i) * VV;
+        for (int r = ty; r < 32; r += 8) {
+            const long a = a0 + r, b = b0 + tx;
+            if (a < V && b < V) {
+                const double d = dab[r][tx] - dba[tx][r];
+                Rij[a * V + b] += d;
+                Rji[a * V + b] -= d;
+            }
+            const long a2 = b0 + r, b2 = a0 + tx;
+            if (ta != tb && a2 < V && b2 < V) {
+                const double d = dba[r][tx] - dab[tx][r];
+                Rij[a2 * V + b2] += d;
+                Rji[a2 * V + b2] -= d;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static bool contiguous4(const TV& v) {
+    return v.rank == 4 && v.stride[3] == 1 && v.stride[2] == v.size[3] && v.stride[1] == v.size[2] * v.size[3] &&
+           v.stride[0] == v.size[1] * v.size[2] * v.size[3];
+}
+
+dcsd_status ring_antisym_add(Ctx* c, const TV& X, const TV& R) {
+    const TV views[4] = {perm(X, {0, 2, 1, 3}), perm(X, {2, 0, 1, 3}), perm(X, {0, 2, 3, 1}), perm(X, {2, 0, 3, 1})};
+    const double al[4] = {1.0, -1.0, -1.0, 1.0};
+    const long O = R.size[0], V = R.size[2];
+    const bool fits = contiguous4(X) && contiguous4(R) && R.size[1] == O && R.size[3] == V && X.size[0] == O &&
+                      X.size[1] == V && X.size[2] == O && X.size[3] == V && O < (1l << 20) && V < (1l << 20);
+    if (!fits) return axpy4(c, 4, al, views, R);
+    if (c->rec) record_axpy4(c, 4, al, views, R);
+    const long nt = (V + 31) / 32, work = O * (O - 1) / 2 * (nt * (nt + 1) / 2);
+    if (work == 0) return DCSD_OK;
+    if (c->trace) trace_begin(c, "ring_antisym n=" + std::to_string(O * O * V * V));
+    k_ring_antisym<<<(unsigned)std::max<long>(1, std::min<long>(work, (long)c->num_sms * 16)), 256, 0, c->stream>>>(
+        X.p, R.p, (int)O, (int)V);
+    trace_end(c);
+    return launch_check(c, "ring_antisym");
+}
+
+// R[i][j][a][b] += X[j][b][i][a] for X [O][V][O][V] and R [O][O][V][V], both
+// contiguous: 32 x 32 (b, a) tiles read along a and written along b through
+// shared memory.  Work items: (i, j) and a pair of tiles.
+__global__ void __launch_bounds__(256) k_add_swapped(const double* __restrict__ X, double* __restrict__ R, int O,
+                                                     int V) {
+    __shared__ double t[32][33];
+    const int nt = (V + 31) / 32;
+    const long ntt = (long)nt * nt, nw = (long)O * O * ntt;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long OV = (long)O * V, VV = (long)V * V;
+    for (long w = blockIdx.x; w < nw; w += gridDim.x) {
+        const long ij = w / ntt, tt = w - ij * ntt;
+        const long i = ij / O, j = ij - i * O;
+        const int a0 = 32 * (int)(tt / nt), b0 = 32 * (int)(tt % nt);
+        const double* Xji = X + j * V * OV + i * V;  // X[j][b][i][a] at b * OV + a
+        for (int r = ty; r < 32; r += 8) {
+            const long b = b0 + r, a = a0 + tx;
+            t[r][tx] = (a < V && b < V) ? Xji[b * OV + a] : 0.0;
+        }
+        __syncthreads();
+        double* Rij = R + (i * O + j) * VV;
+        for (int r = ty; r < 32; r += 8) {
+            const long a = a0 + r, b = b0 + tx;
+            if (a < V && b < V) Rij[a * V + b] += t[tx][r];
+        }
+        __syncthreads();
+    }
+}
+
+dcsd_status add_swapped(Ctx* c, const TV& X, const TV& R) {
+    const long O = R.size[0], V = R.size[2];
+    const bool fits = contiguous4(X) && contiguous4(R) && R.size[1] == O && R.size[3] == V && X.size[0] == O &&
+                      X.size[1] == V && X.size[2] == O && X.size[3] == V && O < (1l << 20) && V < (1l << 20);
+    if (!fits) return axpy_view(c, 1.0, perm(X, {2, 0, 3, 1}), 1.0, R);
+    if (c->rec) {
+        TapeOp op;
+        op.type = OP_AXPY;
+        op.alpha = 1.0;
+        op.beta = 1.0;
+        op.A = perm(X, {2, 0, 3, 1});
+        op.C = R;
+        rec_push(c, std::move(op));
+    }
+    const long nt = (V + 31) / 32, work = O * O * nt * nt;
+    if (work == 0) return DCSD_OK;
+    if (c->trace) trace_begin(c, "add_swapped n=" + std::to_string(O * O * V * V));
+    k_add_swapped<<<(unsigned)std::max<long>(1, std::min<long>(work, (long)c->num_sms * 16)), 256, 0, c->stream>>>(
+        X.p, R.p, (int)O, (int)V);
+    trace_end(c);
+    return launch_check(c, "add_swapped");
 }
 
 // dots of one vector with up to 16 others in a single pass (contiguous)

@@ -217,6 +217,13 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
     // C-condition (2D methods; zero in the CAS case)
     if (method_fr(method)) DCSD_TRY(set_fixed_amplitude(c, ref, method_fr_value(method)));
     else DCSD_TRY(apply_c_condition(c, ref));
+    // t2 is final: the tensor-core operand packs of t2 views copy from its
+    // BF16 image (dropped on every return)
+    struct ImageScope {
+        Ctx* c;
+        ~ImageScope() { c->t2img_src = nullptr; }
+    } image_scope{c};
+    if (prec != DCSD_PREC_FP64) DCSD_TRY(t2_image(c, nsplit));
 
     TV B = view(c->B, {X, n, n});
     TV Bov = sub(sub(B, 1, 0, O), 2, nc, V);
@@ -410,14 +417,11 @@ dcsd_status residual_union(Ctx* c, int ref, int method, int prec) {
                 }
                 if (sg == sp) {
                     // R += P(ij)P(ab) X  (one pass)
-                    const TV views[4] = {perm(Xacc, {0, 2, 1, 3}), perm(Xacc, {2, 0, 1, 3}),
-                                         perm(Xacc, {0, 2, 3, 1}), perm(Xacc, {2, 0, 3, 1})};
-                    const double al[4] = {1.0, -1.0, -1.0, 1.0};
-                    DCSD_TRY(axpy4(c, 4, al, views, blk(R2, sg)));
+                    DCSD_TRY(ring_antisym_add(c, Xacc, blk(R2, sg)));
                 } else if (sg == 0) {
                     DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {0, 2, 1, 3}), 1.0, blk(R2, 2)));
                 } else {
-                    DCSD_TRY(axpy_view(c, 1.0, perm(Xacc, {2, 0, 3, 1}), 1.0, blk(R2, 2)));
+                    DCSD_TRY(add_swapped(c, Xacc, blk(R2, 2)));
                 }
             }
         // mixed-spin pairs of the alpha-beta block

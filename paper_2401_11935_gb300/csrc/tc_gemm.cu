@@ -722,6 +722,267 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
     }
 }
 
+// 8 consecutive BF16 values from element e0 of a 16-byte aligned array that
+// extends to the next multiple of 8 elements past them: one aligned 16-byte
+// load, or two and a shift by e0 % 8 elements
+__device__ __forceinline__ uint4 load8_bf16(const uint16_t* base, long e0) {
+    const int m = (int)(e0 & 7);
+    const uint4* p = (const uint4*)(base + (e0 - m));
+    const uint4 A = p[0];
+    if (m == 0) return A;
+    const uint4 B = p[1];
+    const uint32_t w[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+    const int h = m >> 1;
+    uint32_t o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t lo = h == 0 ? w[q] : h == 1 ? w[q + 1] : h == 2 ? w[q + 2] : w[q + 3];
+        const uint32_t hi = h == 0 ? w[q + 1] : h == 1 ? w[q + 2] : h == 2 ? w[q + 3] : w[q + 4];
+        o[q] = (m & 1) ? __funnelshift_r(lo, hi, 16) : lo;
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// The same packing from the BF16 image of the source (plane p = split part
+// p of every element, planes `plane` elements apart): the parts are copied,
+// so the packed operand is identical to the one k_pack makes from FP64.
+// For sources with a unit-stride row mode (enumerated fastest): eight
+// consecutive rows of one k that form one run of that mode are read as one
+// 16-byte load (load8_bf16) and spread over the tile in shared memory.
+// img points at the source's first element in plane 0 (img - imgbase is the
+// plane's start, 16-byte aligned).
+template <int TR, int TK>
+__global__ void __launch_bounds__(256) k_pack_img(PackArgs a, const uint16_t* img, long plane, int nplanes,
+                                                  long imgbase) {
+    static_assert(TR % 8 == 0, "row groups of 8");
+    __shared__ uint16_t tile[3][TR][TK + 2];
+    __shared__ long roff[TR], rdst[TR], koff[TK];
+    __shared__ int rrun[TR / 8];
+    const long ntr = (a.rows + TR - 1) / TR, ntk = (a.Kp + TK - 1) / TK;
+    const long ldd = a.ldd;
+    const int np = nplanes < 3 ? nplanes : 3;
+    for (long t = blockIdx.x; t < ntr * ntk; t += gridDim.x) {
+        const long r0 = (a.kfast ? t / ntk : t % ntr) * TR, k0 = (a.kfast ? t % ntk : t / ntr) * TK;
+        for (int x = threadIdx.x; x < TR + TK; x += blockDim.x) {
+            if (x < TR) {
+                const long r = r0 + x;
+                long o = -1, d = -1;
+                if (r < a.rows) {
+                    if (a.rtab) {
+                        o = a.rtab[r];
+                        d = r;
+                    } else {
+                        unsigned u = (unsigned)r;
+                        long so = 0, dr = 0;
+                        bool ok = true;
+#pragma unroll
+                        for (int j = kMaxMode - 1; j >= 0; --j) {
+                            if (j < a.nr) {
+                                const unsigned sz = (unsigned)a.r_size[j];
+                                const unsigned qq = u / sz, ix = u - qq * sz;
+                                so += (long)ix * a.r_s[j];
+                                dr += (long)ix * a.r_d[j];
+                                if (j == a.rv_pos && (long)ix >= a.rvalid) ok = false;
+                                u = qq;
+                            }
+                        }
+                        d = dr;
+                        if (ok) o = so;
+                    }
+                }
+                roff[x] = o;
+                rdst[x] = d;
+            } else {
+                const int kk = x - TR;
+                const long k = k0 + kk;
+                long o = -1;
+                if (k < a.K) {
+                    const unsigned ku = (unsigned)k;
+                    if (a.nk == 0 || (long)(ku % (unsigned)a.k_size[a.nk - 1]) < a.kvalid)
+                        o = decomp1_u32(ku, a.nk, a.k_size, a.k_s);
+                }
+                koff[kk] = o;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < TR / 8) {
+            const int g = threadIdx.x;
+            int run = !a.kfast && roff[8 * g] >= 0;
+            for (int q = 1; q < 8 && run; ++q) run = roff[8 * g + q] == roff[8 * g] + q;
+            rrun[g] = run;
+        }
+        __syncthreads();
+        if (!a.kfast) {
+            // consecutive threads: consecutive row groups of one k
+            for (int e = threadIdx.x; e < (TR / 8) * TK; e += 256) {
+                const int g = e % (TR / 8), kk = e / (TR / 8);
+                const long ko = koff[kk];
+                if (ko >= 0 && rrun[g]) {
+                    for (int p = 0; p < np; ++p) {
+                        const uint4 v = load8_bf16(img - imgbase + p * plane, imgbase + roff[8 * g] + ko);
+                        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) tile[p][8 * g + q][kk] = (uint16_t)(w[q >> 1] >> (16 * (q & 1)));
+                    }
+                } else {
+                    for (int q = 0; q < 8; ++q) {
+                        const long ro = roff[8 * g + q];
+                        const bool in = ro >= 0 && ko >= 0;
+                        for (int p = 0; p < np; ++p) tile[p][8 * g + q][kk] = in ? img[p * plane + ro + ko] : (uint16_t)0;
+                    }
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int e = threadIdx.x; e < TR * TK; e += 256) {
+                const int kk = e % TK, rr = e / TK;
+                const long ro = roff[rr], ko = koff[kk];
+                const bool in = ro >= 0 && ko >= 0;
+                for (int p = 0; p < np; ++p) tile[p][rr][kk] = in ? img[p * plane + ro + ko] : (uint16_t)0;
+            }
+        }
+        __syncthreads();
+        constexpr int G = TK / 8;
+        for (int it = threadIdx.x; it < TR * G; it += 256) {
+            const int g = it % G, rr = it / G;
+            const long r = rdst[rr];
+            if (r < 0) continue;
+            __nv_bfloat16* d = a.kbs > 0 ? a.dst + (k0 / 64) * a.kbs + r * 64 + g * 8 : a.dst + r * ldd + k0 + g * 8;
+            for (int sg = 0; sg < a.nseg; ++sg) {
+                const uint16_t* v = &tile[a.pat[sg]][rr][g * 8];
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = (uint32_t)v[2 * q] | ((uint32_t)v[2 * q + 1] << 16);
+                *(uint4*)(d + (long)sg * a.segs) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Packing from the BF16 image of a source contiguous along its innermost k
+// mode (rows in packed order): one warp per (row, 2048 consecutive k), eight
+// k per lane and step.  The row offset is decomposed once per item and the
+// k mode indices are advanced, not recomputed.  Eight k inside one run of the
+// innermost mode are one 16-byte read (load8_bf16), others are gathered one
+// by one; each segment leaves as one 16-byte store.  img: the source's first
+// element in plane 0 (plane p = part p, `plane` elements further); imgbase:
+// its element index in the plane (img - imgbase: the plane's aligned start).
+__global__ void __launch_bounds__(256) k_pack_rows_img(PackArgs a, const uint16_t* img, long plane, int nplanes,
+                                                       long imgbase) {
+    constexpr long KCH = 2048;
+    const int lane = threadIdx.x & 31;
+    const long nkc = (a.Kp + KCH - 1) / KCH;
+    const long nitems = a.rows * nkc;
+    const long wstride = (long)gridDim.x * (blockDim.x >> 5);
+    const int nk = a.nk;
+    const long kin = nk > 0 ? a.k_size[nk - 1] : 1;
+    const bool unit = nk > 0 && a.k_s[nk - 1] == 1;
+    const int np = nplanes < 3 ? nplanes : 3;
+    int used = 0;
+    for (int sg = 0; sg < a.nseg; ++sg) used |= 1 << a.pat[sg];
+    for (long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nitems; w += wstride) {
+        const long r = w / nkc, kb = (w - r * nkc) * KCH, ke = kb + KCH < a.Kp ? kb + KCH : a.Kp;
+        long ro = -1;
+        if (a.rtab) {
+            ro = a.rtab[r];
+        } else {
+            unsigned u = (unsigned)r;
+            long so = 0;
+            bool ok = true;
+#pragma unroll
+            for (int j = kMaxMode - 1; j >= 0; --j) {
+                if (j < a.nr) {
+                    const unsigned sz = (unsigned)a.r_size[j];
+                    const unsigned qq = u / sz, ix = u - qq * sz;
+                    so += (long)ix * a.r_s[j];
+                    if (j == a.rv_pos && (long)ix >= a.rvalid) ok = false;
+                    u = qq;
+                }
+            }
+            if (ok) ro = so;
+        }
+        long k0 = kb + 8 * lane;
+        long idx[kMaxMode];
+        {
+            unsigned u = (unsigned)(k0 < a.K ? k0 : 0);
+#pragma unroll
+            for (int j = kMaxMode - 1; j >= 0; --j) {
+                idx[j] = 0;
+                if (j < nk) {
+                    const unsigned sz = (unsigned)a.k_size[j];
+                    const unsigned qq = u / sz;
+                    idx[j] = (long)(u - qq * sz);
+                    u = qq;
+                }
+            }
+        }
+        for (; k0 < ke; k0 += 256) {
+            long off = 0;
+#pragma unroll
+            for (int j = 0; j < kMaxMode; ++j)
+                if (j < nk) off += idx[j] * a.k_s[j];
+            const long in0 = nk > 0 ? idx[nk - 1] : 0;
+            const bool run = ro >= 0 && unit && k0 + 8 <= a.K && in0 + 8 <= kin && in0 + 8 <= a.kvalid;
+            uint4 v[3] = {};
+            if (run) {
+                for (int p = 0; p < np; ++p)
+                    if (used & (1 << p)) v[p] = load8_bf16(img - imgbase + p * plane, imgbase + ro + off);
+            } else {
+                uint32_t wv[3][4] = {};
+                long id[kMaxMode];
+#pragma unroll
+                for (int j = 0; j < kMaxMode; ++j) id[j] = idx[j];
+                for (int q = 0; q < 8; ++q) {
+                    const long k = k0 + q;
+                    if (ro >= 0 && k < a.K && (nk == 0 || id[nk - 1] < a.kvalid)) {
+                        long o = ro;
+#pragma unroll
+                        for (int j = 0; j < kMaxMode; ++j)
+                            if (j < nk) o += id[j] * a.k_s[j];
+                        for (int p = 0; p < np; ++p)
+                            if (used & (1 << p)) wv[p][q >> 1] |= (uint32_t)img[p * plane + o] << (16 * (q & 1));
+                    }
+                    for (int j = nk - 1; j >= 0; --j) {
+                        if (++id[j] < a.k_size[j]) break;
+                        id[j] = 0;
+                    }
+                }
+                for (int p = 0; p < 3; ++p) v[p] = make_uint4(wv[p][0], wv[p][1], wv[p][2], wv[p][3]);
+            }
+            __nv_bfloat16* d = a.kbs > 0 ? a.dst + (k0 / 64) * a.kbs + r * 64 + (k0 & 63) : a.dst + r * a.ldd + k0;
+            for (int sg = 0; sg < a.nseg; ++sg) *(uint4*)(d + (long)sg * a.segs) = v[a.pat[sg]];
+            // the mode indices of k0 + 256 (innermost first, carries outward)
+            if (nk > 0 && k0 + 256 < a.K) {
+                idx[nk - 1] += 256;
+                for (int j = nk - 1; j > 0; --j) {
+                    if (idx[j] < a.k_size[j]) break;
+                    const long qq = idx[j] / a.k_size[j];
+                    idx[j] -= qq * a.k_size[j];
+                    idx[j - 1] += qq;
+                }
+            }
+        }
+    }
+}
+
+// plane p of the image = part p of the split of every element (as k_pack
+// computes it: FP64 -> FP32, then hi, mid, lo)
+__global__ void k_t2_image(const double* __restrict__ t2, long n, long plane, int nplanes, uint16_t* __restrict__ img) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; 2 * i < n; i += (long)gridDim.x * blockDim.x) {
+        if (2 * i + 1 < n) {
+            const double2 v = *(const double2*)(t2 + 2 * i);
+            const float x0 = f64_to_f32(v.x), x1 = f64_to_f32(v.y);
+            for (int p = 0; p < nplanes; ++p)
+                *(uint32_t*)(img + p * plane + 2 * i) = (uint32_t)__bfloat16_as_ushort(split_part(x0, p)) |
+                                                          ((uint32_t)__bfloat16_as_ushort(split_part(x1, p)) << 16);
+        } else {
+            const float x0 = f64_to_f32(t2[2 * i]);
+            for (int p = 0; p < nplanes; ++p) img[p * plane + 2 * i] = __bfloat16_as_ushort(split_part(x0, p));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -850,6 +1111,9 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
     // has that mode enumerated fastest, so each tile reads contiguous runs
     int order[kMaxMode];
     for (int i = 0; i < nr; ++i) order[i] = i;
+    bool rowcontig = false;  // some row mode has unit stride
+    for (int i = 0; i < nr && !rtab; ++i)
+        if (std::labs(rs[i]) == 1 && rsz[i] > 1) rowcontig = true;
     if (!rtab && !a.kfast && nr >= 2) {
         int js = -1;
         for (int i = 0; i < nr; ++i)
@@ -881,15 +1145,36 @@ static dcsd_status pack(Ctx* c, const double* src, int nr, const long* rsz, cons
     const int TR = 64, TK = 64;
     long tiles = ((rows + TR - 1) / TR) * (Kp / TK);
     unsigned g = (unsigned)std::max<long>(1, std::min<long>(tiles, (long)c->num_sms * 8));
+    // a view of t2 while its BF16 image holds every part the segments use:
+    // copy the parts from the image (the same offsets address it)
+    const uint16_t* img = nullptr;
+    if (!c->pack_generic && c->t2img_src && src >= c->t2img_src && src < c->t2img_src + c->t2img_len) {
+        img = c->t2img + (src - c->t2img_src);
+        for (int i = 0; i < nseg; ++i)
+            if (pat[i] < 0 || pat[i] >= c->t2img_planes) img = nullptr;
+    }
     prof_begin(c, DCSD_PROF_PACK);
     if (c->trace) {
         const std::string label = "pack " + c->cur_spec + " rows=" + std::to_string(rows) + " K=" + std::to_string(K) +
-                                  " kfast=" + std::to_string(a.kfast);
+                                  " kfast=" + std::to_string(a.kfast) + (img && (a.kfast || rowcontig) ? " img" : "");
         if (c->trace_seq) fprintf(stderr, "[dcsd pack #%d] %s\n", c->pack_seq, label.c_str());
         trace_begin(c, label);
     }
     ++c->pack_seq;
-    k_pack<64, 64><<<g, 256, 0, c->stream>>>(a);
+    if (img && a.kfast) {
+        // rows in packed order, source contiguous along k: warp per row run
+        const long items = rows * ((Kp + 2047) / 2048);
+        const unsigned gr = (unsigned)std::max<long>(1, std::min<long>((items + 7) / 8, (long)c->num_sms * 16));
+        k_pack_rows_img<<<gr, 256, 0, c->stream>>>(a, img, c->t2img_plane, c->t2img_planes,
+                                                    (long)(src - c->t2img_src));
+    } else if (img && rowcontig) {
+        // (without a unit-stride row mode the tile's reads are scattered,
+        // and 2-byte reads waste more of each sector than 8-byte ones)
+        k_pack_img<64, 64><<<g, 256, 0, c->stream>>>(a, img, c->t2img_plane, c->t2img_planes,
+                                                     (long)(src - c->t2img_src));
+    } else {
+        k_pack<64, 64><<<g, 256, 0, c->stream>>>(a);
+    }
     trace_end(c);
     prof_end(c, DCSD_PROF_PACK);
     return launch_check(c, "tc_pack");
@@ -1102,6 +1387,32 @@ static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* r
     }
     e->pc_tick[slot] = ++e->pc_clock;
     out = e->pc[slot].p;
+    return DCSD_OK;
+}
+
+dcsd_status t2_image(Ctx* c, int nsplit) {
+    c->t2img_src = nullptr;
+    const long n = 3 * c->O * c->O * c->V * c->V;
+    const long plane = round_up(n, 8);
+    const int np = std::max(1, std::min(3, nsplit));
+    const size_t need = (size_t)np * plane;
+    if (c->t2img_cap < need) {
+        if (c->t2img) cudaFree(c->t2img);
+        c->t2img = nullptr;
+        c->t2img_cap = 0;
+        DCSD_CUDA(c, cudaMalloc((void**)&c->t2img, need * sizeof(uint16_t)));
+        c->t2img_cap = need;
+    }
+    if (c->trace) trace_begin(c, "t2 image planes=" + std::to_string(np));
+    const long pairs = (n + 1) / 2;
+    k_t2_image<<<(unsigned)std::max<long>(1, std::min<long>((pairs + 255) / 256, (long)c->num_sms * 16)), 256, 0,
+                 c->stream>>>(c->t2, n, plane, np, c->t2img);
+    trace_end(c);
+    DCSD_TRY(launch_check(c, "t2_image"));
+    c->t2img_src = c->t2;
+    c->t2img_len = n;
+    c->t2img_plane = plane;
+    c->t2img_planes = np;
     return DCSD_OK;
 }
 
