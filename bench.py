@@ -38,12 +38,11 @@ METRIC = "2D-DCSD s/iteration & ladder TFLOP/s vs peak; mixed vs FP64 at 1e-6 Eh
 UNIT = "s/iteration"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 72 ladder
-# GEMM launches (36 producer, 34 scatter consumer, 2 G-pass consumer) of one
+# dram__bytes_read.sum + dram__bytes_write.sum per ladder GEMM launch of one
 # 30+2 / 500 / 1500 BF16 residual, from a one-pass ncu capture of this
-# benchmark with the K-blocked ladder operands; set to None whenever the
-# ladder kernels change until a new capture replaces it
-LADDER_DRAM_BYTES_PER_LAUNCH = 7.476e9
+# benchmark; None until a capture of the current ladder kernels replaces it
+# (the value is tied to the kernels it was measured on)
+LADDER_DRAM_BYTES_PER_LAUNCH = None
 
 
 def ladder_flops(nc, nv, X):

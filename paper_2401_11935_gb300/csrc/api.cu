@@ -333,6 +333,8 @@ extern "C" dcsd_status dcsd_init(dcsd_ctx** out, const dcsd_dims* d, const doubl
         c->tc_multicast = !(mc && mc[0] == '0');
         const char* pg = getenv("DCSD_PACK_GENERIC");
         c->pack_generic = pg && pg[0] == '1';
+        const char* ls = getenv("DCSD_LADDER_SA");
+        c->ladder_sa = !(ls && ls[0] == '0');
     }
     c->nc = d->n_c;
     c->nv = d->n_v;

@@ -176,6 +176,9 @@ struct Ctx {
     // operand packs: the tiled FP64 kernel only, without the t2 image and the
     // row kernel (DCSD_PACK_GENERIC=1; both give identical operands)
     bool pack_generic = false;
+    // tensor-core ladder in symmetric / antisymmetric form over the (c <= d)
+    // pairs (DCSD_LADDER_SA=0 selects the contraction over all (c, d))
+    bool ladder_sa = true;
 
     MTables* mt[2] = {};          // per reference
     TcEngine* tc = nullptr;

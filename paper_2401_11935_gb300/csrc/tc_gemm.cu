@@ -202,6 +202,7 @@ struct TcEpi {
     //         s = 0,1 (same spin): R[s][ij][a][b] += v, R[s][ij][b][a] -= v
     //         s = 2 (ab):           R[2][ij][a][b] += v
     //         s = 3 (ab, (c,d) exchanged): R[2][ij][b][a] += v  (b > a)
+    //         s = 4, 5 (ab, S+ and S- of the symmetric / antisymmetric form)
     long a0, OO, VV;
     long O;
     const int* rowcode;     // mode 3: row -> (block << 20 | i << 10 | j); same-spin rows are pairs i < j
@@ -211,6 +212,9 @@ struct TcEpi {
 // ladder consumer scatter of one accumulator element v = W(a,b) for the row
 // (blk, i, j); same-spin blocks hold the pair i < j only and also fill the
 // (j, i) row: R[ij][ab] = -R[ij][ba] = -R[ji][ab] = R[ji][ba]
+// Rows of the symmetric / antisymmetric form (blocks 4 and 5, alpha-beta):
+// S+ adds to R[ij][ab] and R[ij][ba], S- adds to R[ij][ab] and subtracts
+// from R[ij][ba] (S- vanishes at a = b).
 template <typename T>
 __device__ __forceinline__ void ladder_scatter(T* R, int sblk, long ro1, long ro2, long a, long b, long V, T v) {
     if (b < a) return;
@@ -221,6 +225,14 @@ __device__ __forceinline__ void ladder_scatter(T* R, int sblk, long ro1, long ro
         R[ro2 + b * V + a] += v;
     } else if (sblk == 2) {
         R[ro1 + a * V + b] += v;
+    } else if (sblk == 4) {
+        R[ro1 + a * V + b] += v;
+        if (b > a) R[ro1 + b * V + a] += v;
+    } else if (sblk == 5) {
+        if (b > a) {
+            R[ro1 + a * V + b] += v;
+            R[ro1 + b * V + a] -= v;
+        }
     } else if (b > a) {
         R[ro1 + b * V + a] += v;
     }
@@ -606,6 +618,336 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ladder in symmetric / antisymmetric form
+// ---------------------------------------------------------------------------
+// For a <= b and c <= d: M+_ab[cd] = (ac|bd) + (ad|bc), M-_ab[cd] = (ac|bd) -
+// (ad|bc).  With A+[cd] = (t_cd + t_dc) / 2 (t_cc / 2 on the diagonal) and
+// A-[cd] = (t_cd - t_dc) / 2, sum_cd t_cd (ac|bd) = S+ + S- and
+// sum_cd t_cd (bc|ad) = S+ - S-, S+- = sum_{c<=d} A+- M+-: the contraction runs
+// over half of the (c,d) pairs.  The (c <= d) index is compact: row c holds
+// d in [floor8(c), Vp), so that 8 consecutive d stay 16-byte aligned;
+// entries with d < c meet zero amplitudes.
+__host__ __device__ __forceinline__ long sa_koff(long c, long Vp) {
+    const long g = c >> 3, rem = c & 7;
+    return 8 * (g * Vp - 4 * g * (g - 1)) + rem * (Vp - 8 * g);
+}
+
+constexpr int SA_STAGES = 3;
+constexpr uint32_t SA_TILE = 128 * TC_BK * 2;  // one 128-row operand tile (16 KB)
+
+struct SaArgs {
+    int nkt;              // k-steps over the packed L (segments x L / 64)
+    int nr, Vb, nblk;     // chunk rows a, columns b (b0 = a0), 128-wide c/d blocks
+    int npair;            // (C, D) block pairs with C <= D
+    long ntiles;          // npair x #(r, b') with b' >= r
+    int a0, YP;           // first a; packed rows per orbital (multiple of 128)
+    int V, Vp;
+    long kbs;             // k-block stride of a V tile (vrows * 64)
+    long segstride;       // elements between the segments of a V tile
+    int nseg, pat[6];
+    __nv_bfloat16* Vplus;
+    __nv_bfloat16* Vminus;
+};
+
+// Tile t -> (r, b', C, D): (C, D) fastest, then r, then b' (b' >= r), so
+// that the tiles in flight share the rows of one b and the chunk's few a
+// rows stay in L2 (each b's rows are read from memory once per chunk)
+__device__ __forceinline__ void sa_tile(const SaArgs& a, long t, int& r, int& bb, int& C, int& D) {
+    long u = t / a.npair;
+    int pr = (int)(t - u * a.npair);
+    const long tri = (long)a.nr * (a.nr + 1) / 2;  // b' < nr: r in [0, b']
+    if (u < tri) {
+        bb = 0;
+        while (u >= bb + 1) {
+            u -= bb + 1;
+            ++bb;
+        }
+        r = (int)u;
+    } else {
+        u -= tri;
+        bb = a.nr + (int)(u / a.nr);
+        r = (int)(u % a.nr);
+    }
+    C = 0;
+    while (pr >= a.nblk - C) {
+        pr -= a.nblk - C;
+        ++C;
+    }
+    D = C + pr;
+}
+
+// Producer of the M+ and M- tiles of one chunk of a: tile (a, b, C, D) with
+// b >= a and C <= D, two accumulators acc1 = B_a[C] B_b[D]^T = M_ab[C][D] and
+// acc2 = B_b[C] B_a[D]^T (element (c,d) = (ad|bc)).  tmA / tmB: the packed
+// virtual-virtual DF factors [(x, y)][L] (y padded to YP rows per x), with
+// the A-side and the B-side split patterns, K-blocked.  Pipeline as in
+// k_tc_gemm: warp 0 loads four 16 KB tiles per stage, warp 1 issues the
+// MMAs, eight epilogue warps write M+- (BF16 split parts) at the compact
+// (c <= d) index of V tile row (r, b').
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_ladder_sa(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, SaArgs a,
+                int* err) {
+    constexpr uint32_t STAGE = 4 * SA_TILE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + SA_STAGES * STAGE);
+    uint64_t* empty = full + SA_STAGES;
+    uint64_t* accf = empty + SA_STAGES;
+    uint64_t* acce = accf + 2;
+    uint32_t* tslot = (uint32_t*)(acce + 2);
+    volatile int* issued = (volatile int*)(tslot + 1);
+    volatile int* consumed = issued + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SA_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kEpiWarps);
+        }
+        *issued = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                int r, bb, C, D;
+                sa_tile(a, t, r, bb, C, D);
+                const int xa = (a.a0 + r) * a.YP, xb = (a.a0 + bb) * a.YP;
+                for (int kt = 0; kt < a.nkt; ++kt, ++g) {
+                    const int s = g % SA_STAGES, round = g / SA_STAGES;
+                    if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    // diagonal block (C = D): acc2 = B_b[C] B_a[C]^T uses the same
+                    // two tiles as acc1 with the roles swapped
+                    uint8_t* st = smem + s * STAGE;
+                    if (C == D) {
+                        mbar_expect_tx(&full[s], 2 * SA_TILE);
+                        tma_load_3d(st, &tmA, &full[s], 0, xa + C * 128, kt);            // B_a[C]
+                        tma_load_3d(st + SA_TILE, &tmB, &full[s], 0, xb + D * 128, kt);  // B_b[C]
+                    } else {
+                        mbar_expect_tx(&full[s], STAGE);
+                        tma_load_3d(st, &tmA, &full[s], 0, xa + C * 128, kt);                // B_a[C]
+                        tma_load_3d(st + SA_TILE, &tmB, &full[s], 0, xb + D * 128, kt);      // B_b[D]
+                        tma_load_3d(st + 2 * SA_TILE, &tmA, &full[s], 0, xb + C * 128, kt);  // B_b[C]
+                        tma_load_3d(st + 3 * SA_TILE, &tmB, &full[s], 0, xa + D * 128, kt);  // B_a[D]
+                    }
+                    *issued = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                       ((uint32_t)(TC_BM >> 4) << 24);
+            int g = 0, j = 0;
+            bool ok = true;
+            for (long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++j) {
+                const int buf = j & 1, u = j >> 1;
+                if (u > 0 && !mbar_wait(&acce[buf], (u - 1) & 1)) {
+                    atomicExch(err, 4);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                int r_, bb_, C, D;
+                sa_tile(a, t, r_, bb_, C, D);
+                // second product's operands: B_b[C], B_a[D] (tiles 2, 3), or
+                // for a diagonal block tiles 1 and 0
+                const uint32_t o2a = C == D ? SA_TILE : 2 * SA_TILE, o2b = C == D ? 0u : 3 * SA_TILE;
+                const uint32_t d1 = tmem + (uint32_t)(buf * 256), d2 = d1 + 128;
+                for (int kt = 0; kt < a.nkt; ++kt, ++g) {
+                    const int s = g % SA_STAGES, round = g / SA_STAGES;
+                    if (!mbar_wait(&full[s], round & 1)) {
+                        atomicExch(err, 2);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(d1, smem_desc(base + kk * 32), smem_desc(base + SA_TILE + kk * 32), idesc, acc);
+                        mma_bf16(d2, smem_desc(base + o2a + kk * 32), smem_desc(base + o2b + kk * 32), idesc, acc);
+                    }
+                    mma_commit(&empty[s]);
+                    *consumed = g + 1;
+                }
+                if (ok) mma_commit(&accf[buf]);
+            }
+            if (!ok) {
+                uint64_t* fin = &accf[j & 1];
+                mma_commit(fin);
+                for (int kt = *consumed; kt < *issued; ++kt) mbar_wait(&full[kt % SA_STAGES], (kt / SA_STAGES) & 1);
+            }
+        }
+    } else {
+        // warps 2..9: TMEM lane quarter warp % 4; warps 2..5 take columns
+        // 0..63 of both accumulators, warps 6..9 columns 64..127
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        int j = 0;
+        for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++j) {
+            const int buf = j & 1, u = j >> 1;
+            int r, bb, C, D;
+            sa_tile(a, t, r, bb, C, D);
+            const bool ok = mbar_wait(&accf[buf], u & 1);
+            tc_fence_after();
+            if (!ok) {
+                atomicExch(err, 3);
+                break;
+            }
+            const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256);
+            const long c = (long)C * 128 + 32 * q + lane;
+            const long c8 = c & ~7l, kc = sa_koff(c, a.Vp);
+            const long R = (long)r * a.Vb + bb;  // V tile row
+#pragma unroll 1
+            for (int ch = 2 * h; ch < 2 * h + 2; ++ch) {
+                uint32_t r1[32], r2[32];
+                tmem_ld32(tb + (uint32_t)(ch * 32), r1);
+                tmem_ld32(tb + 128u + (uint32_t)(ch * 32), r2);
+                if (c >= a.V) continue;
+#pragma unroll
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    const long d = (long)D * 128 + ch * 32 + g8 * 8;
+                    if (d < c8 || d >= a.Vp) continue;
+                    const long k = kc + (d - c8);
+                    const long off = (k >> 6) * a.kbs + R * 64 + (k & 63);
+                    float pl[8], mi[8];
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) {
+                        const float v1 = __uint_as_float(r1[g8 * 8 + x]), v2 = __uint_as_float(r2[g8 * 8 + x]);
+                        pl[x] = v1 + v2;
+                        mi[x] = v1 - v2;
+                    }
+                    for (int sg = 0; sg < a.nseg; ++sg) {
+                        uint32_t wp[4], wm[4];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            wp[x] = (uint32_t)__bfloat16_as_ushort(split_part(pl[2 * x], a.pat[sg])) |
+                                    ((uint32_t)__bfloat16_as_ushort(split_part(pl[2 * x + 1], a.pat[sg])) << 16);
+                            wm[x] = (uint32_t)__bfloat16_as_ushort(split_part(mi[2 * x], a.pat[sg])) |
+                                    ((uint32_t)__bfloat16_as_ushort(split_part(mi[2 * x + 1], a.pat[sg])) << 16);
+                        }
+                        *(uint4*)(a.Vplus + off + sg * a.segstride) = make_uint4(wp[0], wp[1], wp[2], wp[3]);
+                        *(uint4*)(a.Vminus + off + sg * a.segstride) = make_uint4(wm[0], wm[1], wm[2], wm[3]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// Stacked S/A amplitudes from t2 (FP64): operand Am rows [same-spin pairs
+// i < j of blocks 0 and 1 (2P); alpha-beta (O^2)] with A-, operand Ap rows
+// [alpha-beta (O^2)] with A+, over the compact (c <= d) index, K-blocked
+// [Kp / 64][rows][64], nseg segments (pattern pat) `seg*` elements apart.
+// Work item: a source row and a 32 x 32 tile of (c, d) with the d tile not
+// below the c tile; both orientations of the tile pass through shared memory.
+struct SaPackArgs {
+    const double* t2;
+    const long* pairoff;   // [2P] offsets of the same-spin pair rows
+    long OO, VV;
+    int P2, V, Vp, ntile;  // 2P, V, Vp, 32-wide tiles over V
+    long Kp;
+    __nv_bfloat16* Am;
+    __nv_bfloat16* Ap;
+    long rowsM, rowsP;     // rows of Am (2P + O^2) and Ap (O^2)
+    int nseg, pat[6];
+};
+
+__global__ void __launch_bounds__(256) k_pack_sa(SaPackArgs a) {
+    __shared__ float tcd[32][33], tdc[32][33];
+    const long ntp = (long)a.ntile * (a.ntile + 1) / 2;
+    const long nsrc = a.P2 + a.OO;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (long w = blockIdx.x; w < nsrc * ntp; w += gridDim.x) {
+        const long src = w / ntp;
+        long tp = w - src * ntp;
+        int tc = 0;
+        while (tp >= a.ntile - tc) {
+            tp -= a.ntile - tc;
+            ++tc;
+        }
+        const int td = tc + (int)tp;
+        const bool ss = src < a.P2;
+        const double* T = a.t2 + (ss ? a.pairoff[src] : 2 * a.OO * a.VV + (src - a.P2) * a.VV);
+        const int c0 = 32 * tc, d0 = 32 * td;
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int c = c0 + rr, d = d0 + tx;
+            tcd[rr][tx] = (c < a.V && d < a.V) ? f64_to_f32(T[(long)c * a.V + d]) : 0.0f;   // t[c0+rr][d0+tx]
+            const int dd = d0 + rr, cc = c0 + tx;
+            tdc[rr][tx] = (dd < a.V && cc < a.V) ? f64_to_f32(T[(long)dd * a.V + cc]) : 0.0f;  // t[d0+rr][c0+tx]
+        }
+        __syncthreads();
+        // threads 0..127: row c = c0 + tid / 4, 8 d from d0 + 8 * (tid % 4)
+        if (threadIdx.x < 128) {
+            const int rr = threadIdx.x >> 2, g = threadIdx.x & 3;
+            const long c = c0 + rr, c8 = c & ~7l, d = d0 + 8 * g;
+            if (c < a.V && d >= c8 && d < a.Vp) {
+                const long k = sa_koff(c, a.Vp) + (d - c8);
+                float mv[8], pv[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const long dx = d + x;
+                    const float tcdv = tcd[rr][8 * g + x], tdcv = tdc[8 * g + x][rr];
+                    const bool valid = dx < a.V && dx >= c;
+                    mv[x] = valid ? 0.5f * (tcdv - tdcv) : 0.0f;
+                    pv[x] = !valid ? 0.0f : dx == c ? 0.5f * tcdv : 0.5f * (tcdv + tdcv);
+                }
+                // Am rows: the same-spin pairs, then the alpha-beta rows
+                const long offM = (k >> 6) * a.rowsM * 64 + src * 64 + (k & 63);
+                for (int sg = 0; sg < a.nseg; ++sg) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        w4[x] = (uint32_t)__bfloat16_as_ushort(split_part(mv[2 * x], a.pat[sg])) |
+                                ((uint32_t)__bfloat16_as_ushort(split_part(mv[2 * x + 1], a.pat[sg])) << 16);
+                    *(uint4*)(a.Am + offM + sg * a.rowsM * a.Kp) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                if (!ss) {
+                    const long rowP = src - a.P2;
+                    const long offP = (k >> 6) * a.rowsP * 64 + rowP * 64 + (k & 63);
+                    for (int sg = 0; sg < a.nseg; ++sg) {
+                        uint32_t w4[4];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x)
+                            w4[x] = (uint32_t)__bfloat16_as_ushort(split_part(pv[2 * x], a.pat[sg])) |
+                                    ((uint32_t)__bfloat16_as_ushort(split_part(pv[2 * x + 1], a.pat[sg])) << 16);
+                        *(uint4*)(a.Ap + offP + sg * a.rowsP * a.Kp) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1009,6 +1351,16 @@ struct TcEngine {
     std::string pc_key[kPackSlots];
     long pc_tick[kPackSlots] = {};
     long pc_clock = 0;
+    // symmetric / antisymmetric ladder: amplitudes A- (same-spin pairs and
+    // alpha-beta rows) and A+ (alpha-beta rows), the M+ and M- tiles of a
+    // chunk, the DF factors packed [(x, y)][L] with the A- and B-side split
+    // patterns, and the consumer row codes
+    Buf sam, sap, svp, svm, sxa, sxb;
+    int* d_code_m = nullptr;
+    int* d_code_p = nullptr;
+    long sa_O = -1;
+    bool sa_attr = false;
+    int sx_nsplit = 0;  // split of the packed DF factors in sxa / sxb (0: none; B never changes)
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -1045,8 +1397,10 @@ dcsd_status tc_init(Ctx* c) {
 void tc_free(Ctx* c) {
     TcEngine* e = c->tc;
     if (!e) return;
-    for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt})
+    for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt, &e->sam, &e->sap, &e->svp, &e->svm, &e->sxa, &e->sxb})
         if (b->p) cudaFree(b->p);
+    if (e->d_code_m) cudaFree(e->d_code_m);
+    if (e->d_code_p) cudaFree(e->d_code_p);
     if (e->d_pairoff) cudaFree(e->d_pairoff);
     if (e->d_rowcode) cudaFree(e->d_rowcode);
     if (e->d_growoff) cudaFree(e->d_growoff);
@@ -1677,6 +2031,212 @@ static std::vector<std::pair<long, long>> ladder_chunks(long V, long Vp, long ro
     return out;
 }
 
+// chunks of a for the symmetric / antisymmetric ladder (dynamic programming
+// over the tile waves): per chunk (r0, nr) the producer runs npair x
+// #(r, b' >= r) tiles of nkx k-steps (two 128 x 128 MMAs per step, about one
+// 128 x 256 step), the consumers GEMMs of rowsM and rowsP rows against
+// nr * (V - r0) columns over nks k-steps
+static std::vector<std::pair<long, long>> ladder_chunks_sa(long V, long rowsM, long rowsP, long nks, long nkx,
+                                                           long npair, long nmax, int sms) {
+    auto waves = [&](long M, long N) {
+        const long bn = N >= 256 ? 256 : 128;
+        const long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + bn - 1) / bn);
+        return (tiles + sms - 1) / sms;
+    };
+    const double launch = 64.0;
+    std::vector<double> best(V + 1, 0.0);
+    std::vector<long> pick(V + 1, 1);
+    for (long r0 = V - 1; r0 >= 0; --r0) {
+        best[r0] = 1e300;
+        const long Vb = V - r0;
+        const long cap = std::min(4 * nmax, std::max(nmax, nmax * V / std::max<long>(1, Vb)));
+        for (long nr = 1; nr <= std::min(cap, V - r0); ++nr) {
+            const long ptiles = npair * (nr * Vb - nr * (nr - 1) / 2);
+            const double cost = (double)((ptiles + sms - 1) / sms) * (double)nkx +
+                                (double)(waves(rowsM, nr * Vb) + waves(rowsP, nr * Vb)) * (double)nks + launch +
+                                best[r0 + nr];
+            if (cost < best[r0]) {
+                best[r0] = cost;
+                pick[r0] = nr;
+            }
+        }
+    }
+    std::vector<std::pair<long, long>> out;
+    for (long r0 = 0; r0 < V; r0 += pick[r0]) out.push_back({r0, pick[r0]});
+    return out;
+}
+
+// R2 += the ladder in symmetric / antisymmetric form (see sa_koff): per chunk
+// of a, k_ladder_sa builds the M+ and M- tiles and two consumer GEMMs
+// contract them with A- (same-spin pairs and alpha-beta rows) and A+
+// (alpha-beta rows), scattering into R2 (codes 0/1/5 and 4 of ladder_scatter).
+static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
+    TcEngine* e = c->tc;
+    const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
+    int nseg, pa[6], pb[6];
+    split_patterns(nsplit, nseg, pa, pb);
+    const long Vp = round_up(V, 8);
+    const long KS = sa_koff(V, Vp), KSp = round_up(KS, TC_BK), KSt = nseg * KSp;
+    const long XP = round_up(X, TC_BK), Xt = nseg * XP;
+    const int nblk = (int)((Vp + 127) / 128);
+    const long YP = (long)nblk * 128;
+    const int npair = nblk * (nblk + 1) / 2;
+    const long P = O * (O - 1) / 2;
+    const long rowsM = 2 * P + O * O, rowsP = O * O;
+    if (V * YP >= (1l << 31) || KSt >= (1l << 31) || O >= 1024) {
+        c->err = "symmetric / antisymmetric ladder: sizes out of range";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    // consumer row codes: A- rows [same-spin pairs; alpha-beta (block 5)],
+    // A+ rows [alpha-beta (block 4)]
+    if (e->sa_O != O) {
+        std::vector<int> cm(rowsM), cp(rowsP);
+        long m = 0;
+        for (int sb = 0; sb < 2; ++sb)
+            for (long i = 0; i < O; ++i)
+                for (long j = i + 1; j < O; ++j) cm[m++] = (sb << 20) | (int)(i << 10) | (int)j;
+        for (long i = 0; i < O; ++i)
+            for (long j = 0; j < O; ++j) {
+                cm[m++] = (5 << 20) | (int)(i << 10) | (int)j;
+                cp[i * O + j] = (4 << 20) | (int)(i << 10) | (int)j;
+            }
+        for (int** pp : {&e->d_code_m, &e->d_code_p})
+            if (*pp) { cudaFree(*pp); *pp = nullptr; }
+        e->sa_O = -1;
+        DCSD_CUDA(c, cudaMalloc((void**)&e->d_code_m, sizeof(int) * rowsM));
+        DCSD_CUDA(c, cudaMalloc((void**)&e->d_code_p, sizeof(int) * rowsP));
+        DCSD_CUDA(c, cudaMemcpy(e->d_code_m, cm.data(), sizeof(int) * rowsM, cudaMemcpyHostToDevice));
+        DCSD_CUDA(c, cudaMemcpy(e->d_code_p, cp.data(), sizeof(int) * rowsP, cudaMemcpyHostToDevice));
+        e->sa_O = O;
+    }
+    // stacked A- and A+ amplitudes (the partial last k-block zeroed first)
+    DCSD_TRY(ensure(c, e->sam, (size_t)rowsM * KSt));
+    DCSD_TRY(ensure(c, e->sap, (size_t)rowsP * KSt));
+    if (KS % TC_BK != 0)
+        for (int sg = 0; sg < nseg; ++sg) {
+            const long k0 = KS / TC_BK * TC_BK;
+            DCSD_CUDA(c, cudaMemsetAsync(e->sam.p + (size_t)sg * rowsM * KSp + (size_t)k0 * rowsM, 0,
+                                         sizeof(__nv_bfloat16) * rowsM * TC_BK, c->stream));
+            DCSD_CUDA(c, cudaMemsetAsync(e->sap.p + (size_t)sg * rowsP * KSp + (size_t)k0 * rowsP, 0,
+                                         sizeof(__nv_bfloat16) * rowsP * TC_BK, c->stream));
+        }
+    {
+        SaPackArgs sp;
+        std::memset(&sp, 0, sizeof(sp));
+        sp.t2 = c->t2;
+        sp.pairoff = e->d_pairoff;
+        sp.OO = O * O;
+        sp.VV = V * V;
+        sp.P2 = (int)(2 * P);
+        sp.V = (int)V;
+        sp.Vp = (int)Vp;
+        sp.ntile = (int)((V + 31) / 32);
+        sp.Kp = KSp;
+        sp.Am = e->sam.p;
+        sp.Ap = e->sap.p;
+        sp.rowsM = rowsM;
+        sp.rowsP = rowsP;
+        sp.nseg = nseg;
+        for (int i = 0; i < 6; ++i) sp.pat[i] = pa[i];
+        const long work = (2 * P + O * O) * ((long)sp.ntile * (sp.ntile + 1) / 2);
+        prof_begin(c, DCSD_PROF_PACK);
+        if (c->trace) trace_begin(c, "pack sa-amplitudes rows=" + std::to_string(rowsM + rowsP) + " K=" + std::to_string(KS));
+        k_pack_sa<<<(unsigned)std::max<long>(1, std::min<long>(work, (long)c->num_sms * 8)), 256, 0, c->stream>>>(sp);
+        trace_end(c);
+        prof_end(c, DCSD_PROF_PACK);
+        DCSD_TRY(launch_check(c, "pack_sa"));
+    }
+    // the virtual-virtual DF factors [(x, y)][L], y padded to YP, with the A-
+    // and B-side split patterns (B never changes: packed once per split)
+    DCSD_TRY(ensure(c, e->sxa, (size_t)V * YP * Xt));
+    DCSD_TRY(ensure(c, e->sxb, (size_t)V * YP * Xt));
+    if (e->sx_nsplit != nsplit) {
+        e->sx_nsplit = 0;
+        long rsz[2] = {V, YP}, rs[2] = {n, 1};
+        long ksz[1] = {X}, ks[1] = {n * n};
+        const long rows = V * YP;
+        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, rows, X, XP, nseg, pa, e->sxa.p, V, 1l << 62,
+                      nullptr, 0, rows * XP, rows * 64));
+        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, rows, X, XP, nseg, pb, e->sxb.p, V, 1l << 62,
+                      nullptr, 0, rows * XP, rows * 64));
+        e->sx_nsplit = nsplit;
+    }
+    // M+ and M- tiles of a chunk (zeroed when allocated: rows b' < r and the
+    // k padding are never written, and must be finite)
+    const long chunk = std::max<long>(1, std::min<long>(V, 16));
+    for (Buf* b : {&e->svp, &e->svm}) {
+        const __nv_bfloat16* old = b->p;
+        DCSD_TRY(ensure(c, *b, (size_t)chunk * V * KSt));
+        if (b->p != old) DCSD_CUDA(c, cudaMemsetAsync(b->p, 0, b->cap * sizeof(__nv_bfloat16), c->stream));
+    }
+    const size_t smem = SA_STAGES * 4 * (size_t)SA_TILE + 2048;
+    if (!e->sa_attr) {
+        DCSD_CUDA(c, cudaFuncSetAttribute(k_ladder_sa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        e->sa_attr = true;
+    }
+    CUtensorMap ma, mb;
+    DCSD_TRY(make_map_kblk(c, &ma, e->sxa.p, V * YP, Xt, 128));
+    DCSD_TRY(make_map_kblk(c, &mb, e->sxb.p, V * YP, Xt, 128));
+    const auto chunks = ladder_chunks_sa(V, rowsM, rowsP, KSt / TC_BK, Xt / TC_BK, npair, chunk, c->num_sms);
+    for (const auto& ck : chunks) {
+        const long r0 = ck.first, nr = ck.second;
+        const long Vb = V - r0, vrows = nr * Vb;
+        SaArgs sa;
+        std::memset(&sa, 0, sizeof(sa));
+        sa.nkt = (int)(Xt / TC_BK);
+        sa.nr = (int)nr;
+        sa.Vb = (int)Vb;
+        sa.nblk = nblk;
+        sa.npair = npair;
+        sa.ntiles = (long)npair * (nr * Vb - nr * (nr - 1) / 2);
+        sa.a0 = (int)r0;
+        sa.YP = (int)YP;
+        sa.V = (int)V;
+        sa.Vp = (int)Vp;
+        sa.kbs = vrows * 64;
+        sa.segstride = vrows * KSp;
+        sa.nseg = nseg;
+        for (int i = 0; i < 6; ++i) sa.pat[i] = pb[i];
+        sa.Vplus = e->svp.p;
+        sa.Vminus = e->svm.p;
+        prof_begin(c, DCSD_PROF_LADDER);
+        if (c->trace) {
+            const std::string label = "tc-ladder sa-producer nr=" + std::to_string(nr) + " Vb=" + std::to_string(Vb) +
+                                      " tiles=" + std::to_string(sa.ntiles) + " Kt=" + std::to_string(Xt);
+            if (c->trace_seq) fprintf(stderr, "[dcsd tc #%d] %s\n", c->tc_seq, label.c_str());
+            trace_begin(c, label);
+        }
+        ++c->tc_seq;
+        k_ladder_sa<<<(unsigned)std::min<long>(sa.ntiles, c->num_sms), kTcThreads, smem, c->stream>>>(ma, mb, sa,
+                                                                                                        e->d_err);
+        trace_end(c);
+        prof_end(c, DCSD_PROF_LADDER);
+        DCSD_TRY(launch_check(c, "ladder_sa"));
+        // consumers: A- x M- and A+ x M+, one launch per split product
+        TcEpi ce;
+        std::memset(&ce, 0, sizeof(ce));
+        ce.mode = 3;
+        ce.alpha = 1.0;
+        ce.C = R2;
+        ce.C32 = (c->r2f_on && R2 == c->R2) ? c->r2f : nullptr;
+        ce.O = O;
+        ce.V = V;
+        ce.Vb = Vb;
+        ce.a0 = r0;
+        ce.OO = O * O;
+        ce.VV = V * V;
+        for (int sp = 0; sp < nseg; ++sp) {
+            ce.rowcode = e->d_code_m;
+            DCSD_TRY(gemm_packed(c, e->sam.p + (size_t)sp * rowsM * KSp, rowsM, e->svm.p + (size_t)sp * vrows * KSp,
+                                 vrows, KSp, ce, 1, 0, true, true));
+            ce.rowcode = e->d_code_p;
+            DCSD_TRY(gemm_packed(c, e->sap.p + (size_t)sp * rowsP * KSp, rowsP, e->svp.p + (size_t)sp * vrows * KSp,
+                                 vrows, KSp, ce, 1, 0, true, true));
+        }
+    }
+    return DCSD_OK;
+}
+
 dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     TcEngine* e = c->tc;
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
@@ -1771,7 +2331,8 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     // (ac|bd) = (bd|ac): per chunk of a only the columns b >= a0 are built
     // and contracted; the (b,a) elements of the alpha-beta block come from the
     // rows with (c,d) exchanged and same-spin blocks are antisymmetric.
-    for (int pass = 0; pass < 2; ++pass) {
+    if (c->ladder_sa) DCSD_TRY(ladder_sa_pass(c, nsplit, R2));
+    for (int pass = c->ladder_sa ? 1 : 0; pass < 2; ++pass) {
         const long R = pass == 0 ? V : O;
         std::vector<std::pair<long, long>> chunks;
         if (pass == 0) chunks = ladder_chunks(V, Vp, rows4, K2t, Xt, chunk, c->num_sms);

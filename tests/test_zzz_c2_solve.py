@@ -56,3 +56,27 @@ def test_c2_fp64_solve_matches_oracle(method):
     assert res.converged and res.max_r < 1e-10
     assert abs(res.E_S - (res.dEA + res.W)) < 1e-12 and abs(res.E_T - (res.dEA - res.W)) < 1e-12
     check_against_element_oracle(s, method, Tn, res.dEA, res.W)
+
+
+def test_c2_fp64_solve_matches_golden_oracle_solve():
+    """The converged 2D-DCSD energies against an independent oracle solve of the
+    same workload (tests/golden/c2_energies.json, written by
+    tests/golden/make_golden.py: the full FP64 oracle with DIIS to max|R| <
+    1e-10): singlet and triplet energies, Delta E_A and W to 1e-10 Eh."""
+    import json
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2401_11935_gb300 as P
+    with open(os.path.join(HERE, "golden", "c2_energies.json")) as f:
+        gold = json.load(f)
+    assert gold["workload"] == "c2"
+    ref = gold["results"]["2D-DCSD"]
+    s = make_system("c2")
+    eng = P.Engine.from_system(s)
+    T, res = eng.solve(method=P.DCSD, ref=0, precision=P.PREC_FP64, tol=1e-11, maxiter=200)
+    eng.close()
+    assert res.converged
+    for key in ("dEA", "W", "E_S", "E_T"):
+        print(key, getattr(res, key) - ref[key])
+        assert abs(getattr(res, key) - ref[key]) < 1e-10, key
