@@ -1361,6 +1361,14 @@ struct TcEngine {
     long sa_O = -1;
     bool sa_attr = false;
     int sx_nsplit = 0;  // split of the packed DF factors in sxa / sxb (0: none; B never changes)
+    // packed operands read from the DF factors B, which never change after
+    // initialisation: kept for the life of the context (key as in
+    // pack_operand), up to kBCacheBytes in all
+    static constexpr size_t kBCacheBytes = 8ul << 30;
+    std::vector<std::pair<std::string, Buf>> bcache;
+    size_t bcache_bytes = 0;
+    Buf pbv;            // the ladder's B_vv [(b,d)][L] for the G pass
+    int pbv_nsplit = 0; // its split (0: not packed)
 };
 
 static dcsd_status ensure(Ctx* c, Buf& b, size_t elems) {
@@ -1397,8 +1405,10 @@ dcsd_status tc_init(Ctx* c) {
 void tc_free(Ctx* c) {
     TcEngine* e = c->tc;
     if (!e) return;
-    for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt, &e->sam, &e->sap, &e->svp, &e->svm, &e->sxa, &e->sxb})
+    for (Buf* b : {&e->pa, &e->pb, &e->pv, &e->pt, &e->sam, &e->sap, &e->svp, &e->svm, &e->sxa, &e->sxb, &e->pbv})
         if (b->p) cudaFree(b->p);
+    for (auto& kv : e->bcache)
+        if (kv.second.p) cudaFree(kv.second.p);
     if (e->d_code_m) cudaFree(e->d_code_m);
     if (e->d_code_p) cudaFree(e->d_code_p);
     if (e->d_pairoff) cudaFree(e->d_pairoff);
@@ -1715,6 +1725,35 @@ static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* r
     bool cached = false;
     for (int k = 0; k < 2; ++k)
         if (src && src == c->pack_cache_src[k]) cached = true;
+    // views of the DF factors: packed once for the life of the context
+    const size_t nB = (size_t)c->X * c->n * c->n;
+    if (src && c->B && src >= c->B && src < c->B + nB) {
+        std::string key = std::to_string((uintptr_t)src) + "|" + std::to_string(nr) + "|" + std::to_string(nk) + "|" +
+                          std::to_string(rows) + "|" + std::to_string(K) + "|" + std::to_string(Kp) + "|" +
+                          std::to_string(nseg);
+        for (int i = 0; i < nr; ++i) key += "|r" + std::to_string(rsz[i]) + ":" + std::to_string(rs[i]);
+        for (int i = 0; i < nk; ++i) key += "|k" + std::to_string(ksz[i]) + ":" + std::to_string(ks[i]);
+        for (int i = 0; i < nseg; ++i) key += "|p" + std::to_string(pat[i]);
+        for (auto& kv : e->bcache)
+            if (kv.first == key) {
+                out = kv.second.p;
+                return DCSD_OK;
+            }
+        const size_t bytes = (size_t)rows * nseg * Kp * sizeof(__nv_bfloat16);
+        if (e->bcache_bytes + bytes <= TcEngine::kBCacheBytes) {
+            Buf b;
+            DCSD_TRY(ensure(c, b, (size_t)rows * nseg * Kp));
+            const dcsd_status st = pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, b.p);
+            if (st != DCSD_OK) {
+                cudaFree(b.p);
+                return st;
+            }
+            e->bcache.push_back({key, b});
+            e->bcache_bytes += bytes;
+            out = b.p;
+            return DCSD_OK;
+        }
+    }
     if (!cached) {
         DCSD_TRY(ensure(c, dflt, (size_t)rows * nseg * Kp));
         DCSD_TRY(pack(c, src, nr, rsz, rs, nk, ksz, ks, rows, K, Kp, nseg, pat, dflt.p));
@@ -2162,7 +2201,8 @@ static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
         e->sx_nsplit = nsplit;
     }
     // M+ and M- tiles of a chunk (zeroed when allocated: rows b' < r and the
-    // k padding are never written, and must be finite)
+    // k padding are never written, and must be finite).  Chunks of up to 16
+    // rows a (32 measured slower: the chunk's a rows no longer stay in L2)
     const long chunk = std::max<long>(1, std::min<long>(V, 16));
     for (Buf* b : {&e->svp, &e->svm}) {
         const __nv_bfloat16* old = b->p;
@@ -2303,12 +2343,15 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
         DCSD_TRY(pack(c, c->t2 + 2 * O * O * V * V, 1, rsz2, rs, 2, ksz, ks2, O * O, K2, K2p, nseg, pa,
                       e->pt.p + (size_t)(2 * P + O * O) * 64, 1l << 62, V, nullptr, 0, ss, kb));
     }
-    // B_vv packed as [(b,d)][L], d padded (constant over the chunk loop)
-    DCSD_TRY(ensure(c, e->pb, (size_t)K2 * Xt));
-    {
+    // B_vv packed as [(b,d)][L], d padded (B never changes: packed once per
+    // split)
+    DCSD_TRY(ensure(c, e->pbv, (size_t)K2 * Xt));
+    if (e->pbv_nsplit != nsplit) {
+        e->pbv_nsplit = 0;
         long rsz[2] = {V, Vp}, rs[2] = {n, 1};
         long ksz[1] = {X}, ks[1] = {n * n};
-        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, K2, X, XP, nseg, pb, e->pb.p, V));
+        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, K2, X, XP, nseg, pb, e->pbv.p, V));
+        e->pbv_nsplit = nsplit;
     }
     const long chunk = std::max<long>(1, std::min<long>(V, 16));
     {
@@ -2365,7 +2408,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
             pe.rowlen = K2p;
             pe.kbs = vrows * 64;
             pe.Vb = Vb;
-            DCSD_TRY(gemm_packed(c, e->pa.p, nr * V, e->pb.p + (size_t)b0 * Vp * Xt, Vb * Vp, Xt, pe));
+            DCSD_TRY(gemm_packed(c, e->pa.p, nr * V, e->pbv.p + (size_t)b0 * Vp * Xt, Vb * Vp, Xt, pe));
             // consumer: rows (s,i,j) x cols (r,b) over (c,d)
             TcEpi ce;
             std::memset(&ce, 0, sizeof(ce));
