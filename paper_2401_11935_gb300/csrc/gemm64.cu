@@ -997,41 +997,6 @@ __device__ __forceinline__ int vir_map(const LayoutArgs& L, int s, int A) {
     return A == 0 ? L.vir_act[s] : A + 1;
 }
 
-// dir = 0: ABI -> union (scatter); dir = 1: union -> ABI (gather)
-__global__ void k_layout(LayoutArgs L, int dir, double* t1, double* t2, double* a1a, double* a1b,
-                         double* a2aa, double* a2bb, double* a2ab) {
-    const long n1 = (long)L.o * L.v, n2 = (long)L.o * L.o * L.v * L.v;
-    const long total = 2 * n1 + 3 * n2;
-    const long O = L.O, V = L.V;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-         e += (long)gridDim.x * blockDim.x) {
-        if (e < 2 * n1) {
-            int s = (int)(e / n1);
-            long r = e - s * n1;
-            int I = (int)(r / L.v), A = (int)(r % L.v);
-            double* abi = (s == 0 ? a1a : a1b) + r;
-            double* un = t1 + ((long)s * O + occ_map(L, s, I)) * V + vir_map(L, s, A);
-            if (dir == 0) *un = *abi; else *abi = *un;
-        } else {
-            long r = e - 2 * n1;
-            int blk = (int)(r / n2);
-            r -= blk * n2;
-            int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
-            int b = (int)(r % L.v);
-            long q = r / L.v;
-            int a = (int)(q % L.v);
-            q /= L.v;
-            int j = (int)(q % L.o);
-            int i = (int)(q / L.o);
-            double* abi = (blk == 0 ? a2aa : blk == 1 ? a2bb : a2ab) + r;
-            long ui = occ_map(L, s1, i), uj = occ_map(L, s2, j);
-            long ua = vir_map(L, s1, a), ub = vir_map(L, s2, b);
-            double* un = t2 + (((blk * O + ui) * O + uj) * V + ua) * V + ub;
-            if (dir == 0) *un = *abi; else *abi = *un;
-        }
-    }
-}
-
 static LayoutArgs layout_args(Ctx* c, int ref) {
     LayoutArgs L;
     L.nc = c->nc; L.o = c->o; L.v = c->v; L.O = c->O; L.V = c->V;
@@ -1040,44 +1005,105 @@ static LayoutArgs layout_args(Ctx* c, int ref) {
     return L;
 }
 
-dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b, const double* T2aa,
-                     const double* T2bb, const double* T2ab) {
-    size_t n1 = 2ul * c->O * c->V, n2 = 3ul * c->O * c->O * c->V * c->V;
-    DCSD_CUDA(c, cudaMemsetAsync(c->t1, 0, n1 * sizeof(double), c->stream));
-    DCSD_CUDA(c, cudaMemsetAsync(c->t2, 0, n2 * sizeof(double), c->stream));
-    LayoutArgs L = layout_args(c, ref);
-    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
-    trace_begin(c, "layout");
-    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 0, c->t1, c->t2, (double*)T1a,
-                                                          (double*)T1b, (double*)T2aa,
-                                                          (double*)T2bb, (double*)T2ab);
-    trace_end(c);
-    return launch_check(c, "unpack_T");
+// Row-wise form of the same maps.  dir = 0: every element of the union
+// arrays is written (the ABI element it holds, zero where none); one block
+// per union doubles row (blk, i', j'), a final block for the singles.
+// dir = 1: every ABI element is gathered from its union position; one block
+// per ABI doubles row (blk, i, j), a final block for the singles.  Index
+// arithmetic is 32-bit within a row (rows of at most 2^31 elements).
+__device__ __forceinline__ int occ_inv(const LayoutArgs& L, int s, int u) {
+    return u < L.nc ? u : (u == L.occ_act[s] ? L.nc : -1);
+}
+__device__ __forceinline__ int vir_inv(const LayoutArgs& L, int s, int u) {
+    return u == L.vir_act[s] ? 0 : (u >= 2 ? u - 1 : -1);
 }
 
-dcsd_status layout_union(Ctx* c, int ref, int dir, double* u1, double* u2, double* const* abi) {
+__global__ void __launch_bounds__(256) k_layout_rows(LayoutArgs L, int dir, double* t1, double* t2, double* a1a,
+                                                      double* a1b, double* a2aa, double* a2bb, double* a2ab) {
+    const int O = L.O, V = L.V, o = L.o, v = L.v;
+    const int nrow = dir == 0 ? 3 * O * O : 3 * o * o;
+    for (int row = blockIdx.x; row <= nrow; row += gridDim.x) {
+        if (row == nrow) {  // singles
+            if (dir == 0) {
+                for (int e = threadIdx.x; e < 2 * O * V; e += blockDim.x) {
+                    const int s = e / (O * V), r = e - s * O * V, ui = r / V, ua = r - ui * V;
+                    const int I = occ_inv(L, s, ui), A = vir_inv(L, s, ua);
+                    t1[e] = (I >= 0 && A >= 0) ? (s == 0 ? a1a : a1b)[I * v + A] : 0.0;
+                }
+            } else {
+                for (int e = threadIdx.x; e < 2 * o * v; e += blockDim.x) {
+                    const int s = e / (o * v), r = e - s * o * v, I = r / v, A = r - I * v;
+                    (s == 0 ? a1a : a1b)[r] = t1[((long)s * O + occ_map(L, s, I)) * V + vir_map(L, s, A)];
+                }
+            }
+            continue;
+        }
+        if (dir == 0) {
+            const int blk = row / (O * O), ui = (row / O) % O, uj = row % O;
+            const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+            const int i = occ_inv(L, s1, ui), j = occ_inv(L, s2, uj);
+            const bool rowok = i >= 0 && j >= 0;
+            double* un = t2 + (long)row * V * V;
+            const double* ab = (blk == 0 ? a2aa : blk == 1 ? a2bb : a2ab) + (rowok ? ((long)i * o + j) * v * v : 0);
+            for (int ua = 0; ua < V; ++ua) {
+                const int a = rowok ? vir_inv(L, s1, ua) : -1;
+                double* ur = un + (long)ua * V;
+                const double* ar = ab + (long)(a >= 0 ? a : 0) * v;
+                for (int ub = threadIdx.x; ub < V; ub += blockDim.x) {
+                    const int b = vir_inv(L, s2, ub);
+                    ur[ub] = (a >= 0 && b >= 0) ? ar[b] : 0.0;
+                }
+            }
+        } else {
+            const int blk = row / (o * o), i = (row / o) % o, j = row % o;
+            const int s1 = blk == 1 ? 1 : 0, s2 = blk == 0 ? 0 : 1;
+            const int ui = occ_map(L, s1, i), uj = occ_map(L, s2, j);
+            const double* un = t2 + (((long)blk * O + ui) * O + uj) * V * V;
+            double* ab = (blk == 0 ? a2aa : blk == 1 ? a2bb : a2ab) + ((long)i * o + j) * v * v;
+            for (int a = 0; a < v; ++a) {
+                const double* ur = un + (long)vir_map(L, s1, a) * V;
+                double* ar = ab + (long)a * v;
+                for (int b = threadIdx.x; b < v; b += blockDim.x) ar[b] = ur[vir_map(L, s2, b)];
+            }
+        }
+    }
+}
+
+static dcsd_status launch_layout(Ctx* c, int ref, int dir, double* u1, double* u2, double* a0, double* a1,
+                                 double* a2, double* a3, double* a4, const char* what) {
     LayoutArgs L = layout_args(c, ref);
-    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
-    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, dir, u1, u2, abi[0], abi[1], abi[2], abi[3], abi[4]);
-    return launch_check(c, "layout_union");
+    const long rows = dir == 0 ? 3l * c->O * c->O : 3l * c->o * c->o;
+    if (rows >= (1l << 30) || (long)c->V * c->V >= (1l << 31)) {
+        c->err = "layout: sizes out of range";
+        return DCSD_ERR_INVALID_ARG;
+    }
+    if (c->trace) trace_begin(c, "layout");
+    k_layout_rows<<<(unsigned)std::min<long>(rows + 1, (long)c->num_sms * 16), 256, 0, c->stream>>>(
+        L, dir, u1, u2, a0, a1, a2, a3, a4);
+    trace_end(c);
+    return launch_check(c, what);
+}
+
+dcsd_status unpack_T(Ctx* c, int ref, const double* T1a, const double* T1b, const double* T2aa,
+                     const double* T2bb, const double* T2ab) {
+    return launch_layout(c, ref, 0, c->t1, c->t2, (double*)T1a, (double*)T1b, (double*)T2aa, (double*)T2bb,
+                         (double*)T2ab, "unpack_T");
+}
+
+// dir = 0: ABI -> union (every union element written: the ABI element it
+// holds, zero elsewhere); dir = 1: union -> ABI (gather)
+dcsd_status layout_union(Ctx* c, int ref, int dir, double* u1, double* u2, double* const* abi) {
+    return launch_layout(c, ref, dir, u1, u2, abi[0], abi[1], abi[2], abi[3], abi[4], "layout_union");
 }
 
 dcsd_status pack_R(Ctx* c, int ref, double* R1a, double* R1b, double* R2aa, double* R2bb,
                    double* R2ab) {
-    LayoutArgs L = layout_args(c, ref);
-    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
-    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 1, c->R1, c->R2, R1a, R1b, R2aa,
-                                                          R2bb, R2ab);
-    return launch_check(c, "pack_R");
+    return launch_layout(c, ref, 1, c->R1, c->R2, R1a, R1b, R2aa, R2bb, R2ab, "pack_R");
 }
 
 dcsd_status pack_T(Ctx* c, int ref, double* T1a, double* T1b, double* T2aa, double* T2bb,
                    double* T2ab) {
-    LayoutArgs L = layout_args(c, ref);
-    long total = 2l * c->o * c->v + 3l * c->o * c->o * c->v * c->v;
-    k_layout<<<grid_for(c, total), 256, 0, c->stream>>>(L, 1, c->t1, c->t2, T1a, T1b, T2aa,
-                                                          T2bb, T2ab);
-    return launch_check(c, "pack_T");
+    return launch_layout(c, ref, 1, c->t1, c->t2, T1a, T1b, T2aa, T2bb, T2ab, "pack_T");
 }
 
 // S = 1 - tau, T = 1 + tau with tau[nc + a][k] = t1[spin][k][a]
