@@ -203,6 +203,7 @@ struct TcEpi {
     //         s = 2 (ab):           R[2][ij][a][b] += v
     //         s = 3 (ab, (c,d) exchanged): R[2][ij][b][a] += v  (b > a)
     //         s = 4, 5 (ab, S+ and S- of the symmetric / antisymmetric form)
+    // mode 6: G-pass scatter of the symmetric / antisymmetric form (C = G)
     long a0, OO, VV;
     long O;
     const int* rowcode;     // mode 3: row -> (block << 20 | i << 10 | j); same-spin rows are pairs i < j
@@ -542,6 +543,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (++bb == epi.Vb) { bb = 0; ++rr; }
                     }
                 }
+            } else if (epi.mode == 6) {
+                // G-pass scatter of the symmetric / antisymmetric form: row m =
+                // (blk, i, j) as in mode 3, column n = (r, b) with k = a0 + r;
+                // G[s][i][j][k][b] at ((s O + i) O + j) O V + k V + b.  Blocks
+                // 0/1 add to their own G block, 4 (S+) adds to G[2] and G[3],
+                // 5 (S-) adds to G[2] and subtracts from G[3]
+                const long m = (long)m0 + 32 * q + lane;
+                const bool rowok = m < epi.M;
+                const int code = rowok ? epi.rowcode[m] : 0;
+                const int sblk = code >> 20, ri = (code >> 10) & 1023, rj = code & 1023;
+                const long OV = epi.O * epi.V;
+                const long g1 = (((long)(sblk < 2 ? sblk : 2) * epi.O + ri) * epi.O + rj) * OV;
+                const long g3 = ((3l * epi.O + ri) * epi.O + rj) * OV;
+#pragma unroll 1
+                for (int ch = ch0; ch < ch1; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+                    if (!rowok) continue;
+                    const long nst = (long)n0 + ch * 32;
+                    long rr = nst / epi.Vb, bb = nst - rr * epi.Vb;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        if (nst + jj < epi.N) {
+                            const long off = (epi.a0 + rr) * epi.V + bb;
+                            const double v = (double)__uint_as_float(r[jj]);
+                            epi.C[g1 + off] += v;
+                            if (sblk == 4) epi.C[g3 + off] += v;
+                            else if (sblk == 5) epi.C[g3 + off] -= v;
+                        }
+                        if (++bb == epi.Vb) { bb = 0; ++rr; }
+                    }
+                }
             } else {
                 const long m = (long)m0 + 32 * q + lane;
                 const bool rowok = m < epi.M;
@@ -641,10 +674,12 @@ constexpr uint32_t SA_TILE = 128 * TC_BK * 2;  // one 128-row operand tile (16 K
 
 struct SaArgs {
     int nkt;              // k-steps over the packed L (segments x L / 64)
-    int nr, Vb, nblk;     // chunk rows a, columns b (b0 = a0), 128-wide c/d blocks
+    int nr, Vb, nblk;     // chunk rows, columns b, 128-wide c/d blocks
     int npair;            // (C, D) block pairs with C <= D
-    long ntiles;          // npair x #(r, b') with b' >= r
-    int a0, YP;           // first a; packed rows per orbital (multiple of 128)
+    long ntiles;          // npair x #(r, b'): b' >= r (ladder) or all (rect)
+    int rect;             // 0: the ladder triangle b' >= r; 1: all (r, b') (G pass)
+    int xa0, xb0;         // orbital of row r = 0 and of column b' = 0
+    int YP;               // packed rows per orbital (multiple of 128)
     int V, Vp;
     long kbs;             // k-block stride of a V tile (vrows * 64)
     long segstride;       // elements between the segments of a V tile
@@ -660,7 +695,10 @@ __device__ __forceinline__ void sa_tile(const SaArgs& a, long t, int& r, int& bb
     long u = t / a.npair;
     int pr = (int)(t - u * a.npair);
     const long tri = (long)a.nr * (a.nr + 1) / 2;  // b' < nr: r in [0, b']
-    if (u < tri) {
+    if (a.rect) {
+        bb = (int)(u / a.nr);
+        r = (int)(u % a.nr);
+    } else if (u < tri) {
         bb = 0;
         while (u >= bb + 1) {
             u -= bb + 1;
@@ -729,7 +767,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
                 int r, bb, C, D;
                 sa_tile(a, t, r, bb, C, D);
-                const int xa = (a.a0 + r) * a.YP, xb = (a.a0 + bb) * a.YP;
+                const int xa = (a.xa0 + r) * a.YP, xb = (a.xb0 + bb) * a.YP;
                 for (int kt = 0; kt < a.nkt; ++kt, ++g) {
                     const int s = g % SA_STAGES, round = g / SA_STAGES;
                     if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
@@ -2109,7 +2147,7 @@ static std::vector<std::pair<long, long>> ladder_chunks_sa(long V, long rowsM, l
 // of a, k_ladder_sa builds the M+ and M- tiles and two consumer GEMMs
 // contract them with A- (same-spin pairs and alpha-beta rows) and A+
 // (alpha-beta rows), scattering into R2 (codes 0/1/5 and 4 of ladder_scatter).
-static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
+static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2, double* G) {
     TcEngine* e = c->tc;
     const long n = c->n, nc = c->nc, O = c->O, V = c->V, X = c->X;
     int nseg, pa[6], pb[6];
@@ -2122,7 +2160,7 @@ static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
     const int npair = nblk * (nblk + 1) / 2;
     const long P = O * (O - 1) / 2;
     const long rowsM = 2 * P + O * O, rowsP = O * O;
-    if (V * YP >= (1l << 31) || KSt >= (1l << 31) || O >= 1024) {
+    if (n * YP >= (1l << 31) || KSt >= (1l << 31) || O >= 1024) {
         c->err = "symmetric / antisymmetric ladder: sizes out of range";
         return DCSD_ERR_INVALID_ARG;
     }
@@ -2185,19 +2223,21 @@ static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
         prof_end(c, DCSD_PROF_PACK);
         DCSD_TRY(launch_check(c, "pack_sa"));
     }
-    // the virtual-virtual DF factors [(x, y)][L], y padded to YP, with the A-
-    // and B-side split patterns (B never changes: packed once per split)
-    DCSD_TRY(ensure(c, e->sxa, (size_t)V * YP * Xt));
-    DCSD_TRY(ensure(c, e->sxb, (size_t)V * YP * Xt));
+    // the DF factors B[L][x][nc + y] as [(x, y)][L] for every orbital x (the
+    // virtual rows serve the ladder, the occupied ones the G pass), y padded
+    // to YP, with the A- and B-side split patterns (B never changes: packed
+    // once per split)
+    const long xrows = n * YP;
+    DCSD_TRY(ensure(c, e->sxa, (size_t)xrows * Xt));
+    DCSD_TRY(ensure(c, e->sxb, (size_t)xrows * Xt));
     if (e->sx_nsplit != nsplit) {
         e->sx_nsplit = 0;
-        long rsz[2] = {V, YP}, rs[2] = {n, 1};
+        long rsz[2] = {n, YP}, rs[2] = {n, 1};
         long ksz[1] = {X}, ks[1] = {n * n};
-        const long rows = V * YP;
-        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, rows, X, XP, nseg, pa, e->sxa.p, V, 1l << 62,
-                      nullptr, 0, rows * XP, rows * 64));
-        DCSD_TRY(pack(c, c->B + nc * n + nc, 2, rsz, rs, 1, ksz, ks, rows, X, XP, nseg, pb, e->sxb.p, V, 1l << 62,
-                      nullptr, 0, rows * XP, rows * 64));
+        DCSD_TRY(pack(c, c->B + nc, 2, rsz, rs, 1, ksz, ks, xrows, X, XP, nseg, pa, e->sxa.p, V, 1l << 62, nullptr,
+                      0, xrows * XP, xrows * 64));
+        DCSD_TRY(pack(c, c->B + nc, 2, rsz, rs, 1, ksz, ks, xrows, X, XP, nseg, pb, e->sxb.p, V, 1l << 62, nullptr,
+                      0, xrows * XP, xrows * 64));
         e->sx_nsplit = nsplit;
     }
     // M+ and M- tiles of a chunk (zeroed when allocated: rows b' < r and the
@@ -2215,63 +2255,76 @@ static dcsd_status ladder_sa_pass(Ctx* c, int nsplit, double* R2) {
         e->sa_attr = true;
     }
     CUtensorMap ma, mb;
-    DCSD_TRY(make_map_kblk(c, &ma, e->sxa.p, V * YP, Xt, 128));
-    DCSD_TRY(make_map_kblk(c, &mb, e->sxb.p, V * YP, Xt, 128));
-    const auto chunks = ladder_chunks_sa(V, rowsM, rowsP, KSt / TC_BK, Xt / TC_BK, npair, chunk, c->num_sms);
-    for (const auto& ck : chunks) {
-        const long r0 = ck.first, nr = ck.second;
-        const long Vb = V - r0, vrows = nr * Vb;
-        SaArgs sa;
-        std::memset(&sa, 0, sizeof(sa));
-        sa.nkt = (int)(Xt / TC_BK);
-        sa.nr = (int)nr;
-        sa.Vb = (int)Vb;
-        sa.nblk = nblk;
-        sa.npair = npair;
-        sa.ntiles = (long)npair * (nr * Vb - nr * (nr - 1) / 2);
-        sa.a0 = (int)r0;
-        sa.YP = (int)YP;
-        sa.V = (int)V;
-        sa.Vp = (int)Vp;
-        sa.kbs = vrows * 64;
-        sa.segstride = vrows * KSp;
-        sa.nseg = nseg;
-        for (int i = 0; i < 6; ++i) sa.pat[i] = pb[i];
-        sa.Vplus = e->svp.p;
-        sa.Vminus = e->svm.p;
-        prof_begin(c, DCSD_PROF_LADDER);
-        if (c->trace) {
-            const std::string label = "tc-ladder sa-producer nr=" + std::to_string(nr) + " Vb=" + std::to_string(Vb) +
-                                      " tiles=" + std::to_string(sa.ntiles) + " Kt=" + std::to_string(Xt);
-            if (c->trace_seq) fprintf(stderr, "[dcsd tc #%d] %s\n", c->tc_seq, label.c_str());
-            trace_begin(c, label);
-        }
-        ++c->tc_seq;
-        k_ladder_sa<<<(unsigned)std::min<long>(sa.ntiles, c->num_sms), kTcThreads, smem, c->stream>>>(ma, mb, sa,
-                                                                                                        e->d_err);
-        trace_end(c);
-        prof_end(c, DCSD_PROF_LADDER);
-        DCSD_TRY(launch_check(c, "ladder_sa"));
-        // consumers: A- x M- and A+ x M+, one launch per split product
-        TcEpi ce;
-        std::memset(&ce, 0, sizeof(ce));
-        ce.mode = 3;
-        ce.alpha = 1.0;
-        ce.C = R2;
-        ce.C32 = (c->r2f_on && R2 == c->R2) ? c->r2f : nullptr;
-        ce.O = O;
-        ce.V = V;
-        ce.Vb = Vb;
-        ce.a0 = r0;
-        ce.OO = O * O;
-        ce.VV = V * V;
-        for (int sp = 0; sp < nseg; ++sp) {
-            ce.rowcode = e->d_code_m;
-            DCSD_TRY(gemm_packed(c, e->sam.p + (size_t)sp * rowsM * KSp, rowsM, e->svm.p + (size_t)sp * vrows * KSp,
-                                 vrows, KSp, ce, 1, 0, true, true));
-            ce.rowcode = e->d_code_p;
-            DCSD_TRY(gemm_packed(c, e->sap.p + (size_t)sp * rowsP * KSp, rowsP, e->svp.p + (size_t)sp * vrows * KSp,
-                                 vrows, KSp, ce, 1, 0, true, true));
+    DCSD_TRY(make_map_kblk(c, &ma, e->sxa.p, xrows, Xt, 128));
+    DCSD_TRY(make_map_kblk(c, &mb, e->sxb.p, xrows, Xt, 128));
+    // pass 0, the ladder: chunks of a (triangle b >= a), scatter into R2;
+    // pass 1, the G intermediate G[s][i][j][k][b] = sum_cd t[ij][cd] (kc|bd)
+    // (s = 3: t with (c,d) exchanged): chunks of occupied k against every b,
+    // scatter into G (zeroed first)
+    DCSD_CUDA(c, cudaMemsetAsync(G, 0, sizeof(double) * 4 * O * O * O * V, c->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<std::pair<long, long>> chunks;
+        if (pass == 0) chunks = ladder_chunks_sa(V, rowsM, rowsP, KSt / TC_BK, Xt / TC_BK, npair, chunk, c->num_sms);
+        else
+            for (long k0 = 0; k0 < O; k0 += chunk) chunks.push_back({k0, std::min(chunk, O - k0)});
+        for (const auto& ck : chunks) {
+            const long r0 = ck.first, nr = ck.second;
+            const long Vb = pass == 0 ? V - r0 : V, vrows = nr * Vb;
+            SaArgs sa;
+            std::memset(&sa, 0, sizeof(sa));
+            sa.nkt = (int)(Xt / TC_BK);
+            sa.nr = (int)nr;
+            sa.Vb = (int)Vb;
+            sa.nblk = nblk;
+            sa.npair = npair;
+            sa.rect = pass;
+            sa.ntiles = pass == 0 ? (long)npair * (nr * Vb - nr * (nr - 1) / 2) : (long)npair * nr * Vb;
+            sa.xa0 = (int)(pass == 0 ? nc + r0 : r0);
+            sa.xb0 = (int)(pass == 0 ? nc + r0 : nc);
+            sa.YP = (int)YP;
+            sa.V = (int)V;
+            sa.Vp = (int)Vp;
+            sa.kbs = vrows * 64;
+            sa.segstride = vrows * KSp;
+            sa.nseg = nseg;
+            for (int i = 0; i < 6; ++i) sa.pat[i] = pb[i];
+            sa.Vplus = e->svp.p;
+            sa.Vminus = e->svm.p;
+            prof_begin(c, DCSD_PROF_LADDER);
+            if (c->trace) {
+                const std::string label = std::string(pass == 0 ? "tc-ladder sa-producer" : "tc-ladder sa-g-producer") +
+                                          " nr=" + std::to_string(nr) + " Vb=" + std::to_string(Vb) +
+                                          " tiles=" + std::to_string(sa.ntiles) + " Kt=" + std::to_string(Xt);
+                if (c->trace_seq) fprintf(stderr, "[dcsd tc #%d] %s\n", c->tc_seq, label.c_str());
+                trace_begin(c, label);
+            }
+            ++c->tc_seq;
+            k_ladder_sa<<<(unsigned)std::min<long>(sa.ntiles, c->num_sms), kTcThreads, smem, c->stream>>>(ma, mb, sa,
+                                                                                                            e->d_err);
+            trace_end(c);
+            prof_end(c, DCSD_PROF_LADDER);
+            DCSD_TRY(launch_check(c, "ladder_sa"));
+            // consumers: A- x M- and A+ x M+, one launch per split product
+            TcEpi ce;
+            std::memset(&ce, 0, sizeof(ce));
+            ce.mode = pass == 0 ? 3 : 6;
+            ce.alpha = 1.0;
+            ce.C = pass == 0 ? R2 : G;
+            ce.C32 = (pass == 0 && c->r2f_on && R2 == c->R2) ? c->r2f : nullptr;
+            ce.O = O;
+            ce.V = V;
+            ce.Vb = Vb;
+            ce.a0 = r0;
+            ce.OO = O * O;
+            ce.VV = V * V;
+            for (int sp = 0; sp < nseg; ++sp) {
+                ce.rowcode = e->d_code_m;
+                DCSD_TRY(gemm_packed(c, e->sam.p + (size_t)sp * rowsM * KSp, rowsM,
+                                     e->svm.p + (size_t)sp * vrows * KSp, vrows, KSp, ce, 1, 0, true, true));
+                ce.rowcode = e->d_code_p;
+                DCSD_TRY(gemm_packed(c, e->sap.p + (size_t)sp * rowsP * KSp, rowsP,
+                                     e->svp.p + (size_t)sp * vrows * KSp, vrows, KSp, ce, 1, 0, true, true));
+            }
         }
     }
     return DCSD_OK;
@@ -2325,6 +2378,18 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
         e->tab_O = O;
         e->tab_V = V;
     }
+    if (c->ladder_sa) {
+        // symmetric / antisymmetric form: ladder and G pass
+        struct PhaseGuardSa {
+            Ctx* c;
+            ~PhaseGuardSa() { c->ladder_phase = 0; c->cur_spec = ""; }
+        } guard_sa{c};
+        c->ladder_phase = 1;
+        c->cur_spec = "ladder";
+        DCSD_TRY(ladder_sa_pass(c, nsplit, R2, G));
+        k_mirror_pairs<<<(unsigned)std::max(1, c->num_sms * 8), 256, 0, c->stream>>>(O, O * V, G);
+        return launch_check(c, "mirror_pairs");
+    }
     // stacked amplitudes [aa pairs; bb pairs; ab; ab~] x (c,d): segment s is
     // the operand at s * rows4 * K2p, stored K-blocked [K2p / 64][rows4][64] so
     // that each TMA box (64 k x a tile of rows) is one contiguous block
@@ -2374,8 +2439,7 @@ dcsd_status ladder_tc(Ctx* c, int nsplit, double* R2, double* G) {
     // (ac|bd) = (bd|ac): per chunk of a only the columns b >= a0 are built
     // and contracted; the (b,a) elements of the alpha-beta block come from the
     // rows with (c,d) exchanged and same-spin blocks are antisymmetric.
-    if (c->ladder_sa) DCSD_TRY(ladder_sa_pass(c, nsplit, R2));
-    for (int pass = c->ladder_sa ? 1 : 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 2; ++pass) {
         const long R = pass == 0 ? V : O;
         std::vector<std::pair<long, long>> chunks;
         if (pass == 0) chunks = ladder_chunks(V, Vp, rows4, K2t, Xt, chunk, c->num_sms);
