@@ -594,6 +594,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tmem_ld32(tbase + (uint32_t)(ch * 32), r);
                     if (!rowok) continue;
                     const long* cb = coffs + (ch - ch0) * 32;
+                    if (epi.mode == 4) {
+                        // FP32 accumulation: all 32 loads of the chunk, then its stores
+                        float oldf[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const long co = cb[jj];
+                            oldf[jj] = co >= 0 ? epi.C32[roff + co] : 0.0f;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const long co = cb[jj];
+                            if (co >= 0) epi.C32[roff + co] = fmaf(alpha, __uint_as_float(r[jj]), oldf[jj]);
+                        }
+                        continue;
+                    }
                     // two halves of 16 columns: all loads of a half, then its stores
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
