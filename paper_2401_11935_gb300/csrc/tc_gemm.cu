@@ -216,26 +216,31 @@ struct TcEpi {
 // Rows of the symmetric / antisymmetric form (blocks 4 and 5, alpha-beta):
 // S+ adds to R[ij][ab] and R[ij][ba], S- adds to R[ij][ab] and subtracts
 // from R[ij][ba] (S- vanishes at a = b).
+// Every target of a launch receives one update (the targets of different
+// rows and columns are distinct; a = b same-spin elements are skipped, their
+// four updates cancel), so the updates are reductions without a returned
+// value: the result equals a read-modify-write and no load is waited for.
 template <typename T>
 __device__ __forceinline__ void ladder_scatter(T* R, int sblk, long ro1, long ro2, long a, long b, long V, T v) {
     if (b < a) return;
     if (sblk < 2) {
-        R[ro1 + a * V + b] += v;
-        R[ro1 + b * V + a] -= v;
-        R[ro2 + a * V + b] -= v;
-        R[ro2 + b * V + a] += v;
+        if (b == a) return;
+        atomicAdd(R + ro1 + a * V + b, v);
+        atomicAdd(R + ro1 + b * V + a, -v);
+        atomicAdd(R + ro2 + a * V + b, -v);
+        atomicAdd(R + ro2 + b * V + a, v);
     } else if (sblk == 2) {
-        R[ro1 + a * V + b] += v;
+        atomicAdd(R + ro1 + a * V + b, v);
     } else if (sblk == 4) {
-        R[ro1 + a * V + b] += v;
-        if (b > a) R[ro1 + b * V + a] += v;
+        atomicAdd(R + ro1 + a * V + b, v);
+        if (b > a) atomicAdd(R + ro1 + b * V + a, v);
     } else if (sblk == 5) {
         if (b > a) {
-            R[ro1 + a * V + b] += v;
-            R[ro1 + b * V + a] -= v;
+            atomicAdd(R + ro1 + a * V + b, v);
+            atomicAdd(R + ro1 + b * V + a, -v);
         }
     } else if (b > a) {
-        R[ro1 + b * V + a] += v;
+        atomicAdd(R + ro1 + b * V + a, v);
     }
 }
 
@@ -567,10 +572,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int jj = 0; jj < 32; ++jj) {
                         if (nst + jj < epi.N) {
                             const long off = (epi.a0 + rr) * epi.V + bb;
+                            // one update per target and launch: reductions
                             const double v = (double)__uint_as_float(r[jj]);
-                            epi.C[g1 + off] += v;
-                            if (sblk == 4) epi.C[g3 + off] += v;
-                            else if (sblk == 5) epi.C[g3 + off] -= v;
+                            atomicAdd(epi.C + g1 + off, v);
+                            if (sblk == 4) atomicAdd(epi.C + g3 + off, v);
+                            else if (sblk == 5) atomicAdd(epi.C + g3 + off, -v);
                         }
                         if (++bb == epi.Vb) { bb = 0; ++rr; }
                     }
@@ -595,17 +601,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (!rowok) continue;
                     const long* cb = coffs + (ch - ch0) * 32;
                     if (epi.mode == 4) {
-                        // FP32 accumulation: all 32 loads of the chunk, then its stores
-                        float oldf[32];
+                        // FP32 accumulation: every element of C32 gets one update
+                        // per launch, as a reduction (no load waited for)
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj) {
                             const long co = cb[jj];
-                            oldf[jj] = co >= 0 ? epi.C32[roff + co] : 0.0f;
-                        }
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            const long co = cb[jj];
-                            if (co >= 0) epi.C32[roff + co] = fmaf(alpha, __uint_as_float(r[jj]), oldf[jj]);
+                            if (co >= 0) atomicAdd(epi.C32 + roff + co, alpha * __uint_as_float(r[jj]));
                         }
                         continue;
                     }
