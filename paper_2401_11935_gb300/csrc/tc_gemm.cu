@@ -600,6 +600,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tmem_ld32(tbase + (uint32_t)(ch * 32), r);
                     if (!rowok) continue;
                     const long* cb = coffs + (ch - ch0) * 32;
+                    if (epi.mode == 0 && epi.beta == 1.0) {
+                        // FP64 accumulation with beta = 1: one update per element
+                        // and launch, as a reduction (old + v, as fma(1, old, v))
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const long co = cb[jj];
+                            if (co >= 0) atomicAdd(epi.C + roff + co, f32_to_f64(alpha * __uint_as_float(r[jj])));
+                        }
+                        continue;
+                    }
                     if (epi.mode == 4) {
                         // FP32 accumulation: every element of C32 gets one update
                         // per launch, as a reduction (no load waited for)
