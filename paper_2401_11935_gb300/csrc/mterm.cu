@@ -755,11 +755,12 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
                     if (d < nx) c2 += fx[d] * G[(long)d * V + b];
                 for (int m = 0; m < nh; ++m)
                     c2 += hcT[m] * to_t<T>(hd[m].base[(long)x * hd[m].sa + (long)b * hd[m].sb]);
-                Rx[b] -= to_f64(Wt * (c2 - tc_of(b, tia, cia, tja, cja)));
+                // one update per element: a reduction (no load waited for)
+                atomicAdd(Rx + b, -to_f64(Wt * (c2 - tc_of(b, tia, cia, tja, cja))));
             } else {
                 const int cls = blk * 16 + (ai << 3) + (aj << 2);
                 const int q[4] = {i, j, x, b};
-                Rx[b] -= W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)));
+                atomicAdd(Rx + b, -(W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)))));
             }
         }
     }
@@ -783,7 +784,7 @@ __global__ void __launch_bounds__(256) k_mterm_doubles_sep(MArgs a, int maxx) {
         const T tja = to_t<T>(tA[j * V + x]), cja = to_t<T>(cA[j * V + x]);
         const int cls = blk * 16 + (ai << 3) + (aj << 2) + (aa << 1) + ab;
         const int q[4] = {i, j, x, b};
-        Rrow[e] -= W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)));
+        atomicAdd(Rrow + e, -(W * (eval_class(a, cls, q) - to_f64(tc_of(b, tia, cia, tja, cja)))));
     }
 }
 
