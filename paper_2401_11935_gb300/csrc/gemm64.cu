@@ -408,12 +408,29 @@ __global__ void __launch_bounds__(256) k_gemv64(GemmArgs g, int vec_is_b) {
         long oa, oc, ob = 0;
         if (vec_is_b) decomp2(o, p.nm, p.m_size, p.m_sa, p.m_sc, oa, oc);
         else { decomp2(o, p.nn, p.n_size, p.n_sb, p.n_sc, ob, oc); oa = 0; }
-        double s = 0.0;
-        for (long k = lane; k < p.K; k += 32) {
+        // four independent partial sums (k, k + 32, k + 64, k + 96), so that
+        // the loads of four elements are in flight at once
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        long k = lane;
+        for (; k + 96 < p.K; k += 128) {
+            long ka0, kb0, ka1, kb1, ka2, kb2, ka3, kb3;
+            decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, ka0, kb0);
+            decomp2(k + 32, p.nk, p.k_size, p.k_sa, p.k_sb, ka1, kb1);
+            decomp2(k + 64, p.nk, p.k_size, p.k_sa, p.k_sb, ka2, kb2);
+            decomp2(k + 96, p.nk, p.k_size, p.k_sa, p.k_sb, ka3, kb3);
+            const double a0 = g.A[oa + ka0], a1 = g.A[oa + ka1], a2 = g.A[oa + ka2], a3 = g.A[oa + ka3];
+            const double b0 = g.B[ob + kb0], b1 = g.B[ob + kb1], b2 = g.B[ob + kb2], b3 = g.B[ob + kb3];
+            s0 = fma(a0, b0, s0);
+            s1 = fma(a1, b1, s1);
+            s2 = fma(a2, b2, s2);
+            s3 = fma(a3, b3, s3);
+        }
+        for (; k < p.K; k += 32) {
             long ka, kb;
             decomp2(k, p.nk, p.k_size, p.k_sa, p.k_sb, ka, kb);
-            s = fma(g.A[oa + ka], g.B[ob + kb], s);
+            s0 = fma(g.A[oa + ka], g.B[ob + kb], s0);
         }
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
         if (lane == 0) {
