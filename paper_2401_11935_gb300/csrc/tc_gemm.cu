@@ -1425,9 +1425,9 @@ struct TcEngine {
     long sa_O = -1;
     bool sa_attr = false;
     int sx_nsplit = 0;  // split of the packed DF factors in sxa / sxb (0: none; B never changes)
-    // packed operands read from the DF factors B, which never change after
-    // initialisation: kept for the life of the context (key as in
-    // pack_operand), up to kBCacheBytes in all
+    // packed operands read from the DF factors B or from J, which never
+    // change after initialisation: kept for the life of the context (key as
+    // in pack_operand), up to kBCacheBytes in all
     static constexpr size_t kBCacheBytes = 8ul << 30;
     std::vector<std::pair<std::string, Buf>> bcache;
     size_t bcache_bytes = 0;
@@ -1789,9 +1789,10 @@ static dcsd_status pack_operand(Ctx* c, const double* src, int nr, const long* r
     bool cached = false;
     for (int k = 0; k < 2; ++k)
         if (src && src == c->pack_cache_src[k]) cached = true;
-    // views of the DF factors: packed once for the life of the context
-    const size_t nB = (size_t)c->X * c->n * c->n;
-    if (src && c->B && src >= c->B && src < c->B + nB) {
+    // views of the DF factors B and of J = (kc|ld), both made at
+    // initialisation and never changed: packed once for the life of the context
+    const size_t nB = (size_t)c->X * c->n * c->n, nJ = (size_t)c->O * c->O * c->V * c->V;
+    if (src && ((c->B && src >= c->B && src < c->B + nB) || (c->J && src >= c->J && src < c->J + nJ))) {
         std::string key = std::to_string((uintptr_t)src) + "|" + std::to_string(nr) + "|" + std::to_string(nk) + "|" +
                           std::to_string(rows) + "|" + std::to_string(K) + "|" + std::to_string(Kp) + "|" +
                           std::to_string(nseg);
