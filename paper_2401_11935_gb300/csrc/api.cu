@@ -114,11 +114,26 @@ __global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V
     }
 }
 
-__global__ void k_maxabs_partial(const double* p, long n, double* part) {
+// max |p[e]| per block; with flag set, a non-finite element also sets
+// *flag = 1 (one pass for the convergence measure and the finiteness check).
+// Four independent loads per thread and step.
+__global__ void k_maxabs_partial(const double* p, long n, double* part, double* flag) {
     __shared__ double sh[256];
     double m = 0.0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(p[e]));
+    bool bad = false;
+    const long stride = (long)gridDim.x * blockDim.x;
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    for (; e + 3 * stride < n; e += 4 * stride) {
+        const double x0 = p[e], x1 = p[e + stride], x2 = p[e + 2 * stride], x3 = p[e + 3 * stride];
+        bad |= !isfinite(x0) || !isfinite(x1) || !isfinite(x2) || !isfinite(x3);
+        m = fmax(fmax(m, fabs(x0)), fmax(fabs(x1), fmax(fabs(x2), fabs(x3))));
+    }
+    for (; e < n; e += stride) {
+        const double x = p[e];
+        bad |= !isfinite(x);
+        m = fmax(m, fabs(x));
+    }
+    if (bad && flag) *flag = 1.0;
     sh[threadIdx.x] = m;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
@@ -171,8 +186,8 @@ static unsigned grid_n(Ctx* c, long n) {
     return (unsigned)std::max<long>(1, std::min(g, cap));
 }
 
-static dcsd_status maxabs(Ctx* c, const double* p, long n, double* out) {
-    k_maxabs_partial<<<512, 256, 0, c->stream>>>(p, n, c->red);
+static dcsd_status maxabs(Ctx* c, const double* p, long n, double* out, double* flag = nullptr) {
+    k_maxabs_partial<<<512, 256, 0, c->stream>>>(p, n, c->red, flag);
     DCSD_TRY(launch_check(c, "maxabs_partial"));
     k_maxabs_final<<<1, 256, 0, c->stream>>>(c->red, 512, out);
     return launch_check(c, "maxabs_final");
@@ -984,9 +999,9 @@ extern "C" dcsd_status dcsd_solve(dcsd_ctx* h, const dcsd_solve_opts* o, int mem
         if (refining && !outer) {
             if ((s = axpy_view(c, -1.0, view(c->defect, {len}), 1.0, Rall)) != DCSD_OK) { status = s; break; }
         }
-        if ((s = maxabs(c, c->R1, len, c->scal + 21)) != DCSD_OK) { status = s; break; }
+        // max|R| and the finiteness flag in one pass
         DCSD_CUDA(c, cudaMemsetAsync(c->scal + 20, 0, sizeof(double), c->stream));
-        if ((s = check_finite(c, c->R1, len, c->scal + 20)) != DCSD_OK) { status = s; break; }
+        if ((s = maxabs(c, c->R1, len, c->scal + 21, c->scal + 20)) != DCSD_OK) { status = s; break; }
         if ((s = sync_scalars(c, 23)) != DCSD_OK) { status = s; break; }
         if (tc_timeout(c)) { status = DCSD_ERR_TIMEOUT; break; }
         const double W = c->hostbuf[0], dE = c->hostbuf[1], rmax = c->hostbuf[21];
