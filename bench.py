@@ -38,12 +38,13 @@ METRIC = "2D-DCSD s/iteration & ladder TFLOP/s vs peak; mixed vs FP64 at 1e-6 Eh
 UNIT = "s/iteration"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 88 ladder
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 90 ladder
 # launches of one 30+2 / 500 / 1500 BF16 residual in symmetric / antisymmetric
-# form (28 M+- producers, 56 consumers, 2 G-pass producers, 2 G-pass
-# consumers), from a one-pass ncu capture of this benchmark; set to None
-# whenever the ladder kernels change until a new capture replaces it
-LADDER_DRAM_BYTES_PER_LAUNCH = 3.864e9
+# form (28 M+- producers and 56 consumers for the ladder, 2 producers and 4
+# consumers for the G intermediate), from a one-pass ncu capture of this
+# benchmark; set to None whenever the ladder kernels change until a new
+# capture replaces it
+LADDER_DRAM_BYTES_PER_LAUNCH = 4.343e9
 
 
 def ladder_flops(nc, nv, X):
