@@ -116,31 +116,32 @@ __global__ void __launch_bounds__(256) k_jacobi_rows(int n, int nc, int O, int V
 
 // max |p[e]| per block; with flag set, a non-finite element also sets
 // *flag = 1 (one pass for the convergence measure and the finiteness check).
-// Four independent loads per thread and step.
+// The max runs on the integer units: with the sign bit cleared, the bit
+// patterns of finite doubles order as their magnitudes, and every Inf or NaN
+// pattern lies above them (exponent all ones), which is the flag's test.
 __global__ void k_maxabs_partial(const double* p, long n, double* part, double* flag) {
-    __shared__ double sh[256];
-    double m = 0.0;
-    bool bad = false;
+    __shared__ unsigned long long sh[256];
+    const unsigned long long* q = (const unsigned long long*)p;
+    const unsigned long long mask = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long m = 0;
     const long stride = (long)gridDim.x * blockDim.x;
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     for (; e + 3 * stride < n; e += 4 * stride) {
-        const double x0 = p[e], x1 = p[e + stride], x2 = p[e + 2 * stride], x3 = p[e + 3 * stride];
-        bad |= !isfinite(x0) || !isfinite(x1) || !isfinite(x2) || !isfinite(x3);
-        m = fmax(fmax(m, fabs(x0)), fmax(fabs(x1), fmax(fabs(x2), fabs(x3))));
+        const unsigned long long x0 = q[e] & mask, x1 = q[e + stride] & mask, x2 = q[e + 2 * stride] & mask,
+                                 x3 = q[e + 3 * stride] & mask;
+        m = max(max(m, x0), max(x1, max(x2, x3)));
     }
-    for (; e < n; e += stride) {
-        const double x = p[e];
-        bad |= !isfinite(x);
-        m = fmax(m, fabs(x));
-    }
-    if (bad && flag) *flag = 1.0;
+    for (; e < n; e += stride) m = max(m, q[e] & mask);
     sh[threadIdx.x] = m;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        if (threadIdx.x < w) sh[threadIdx.x] = max(sh[threadIdx.x], sh[threadIdx.x + w]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) {
+        if (flag && sh[0] >= 0x7FF0000000000000ull) *flag = 1.0;
+        part[blockIdx.x] = __longlong_as_double((long long)sh[0]);
+    }
 }
 
 __global__ void k_maxabs_final(const double* part, int n, double* out) {
