@@ -965,11 +965,20 @@ __global__ void __launch_bounds__(256) k_pack_sa(SaPackArgs a) {
         const bool ss = src < a.P2;
         const double* T = a.t2 + (ss ? a.pairoff[src] : 2 * a.OO * a.VV + (src - a.P2) * a.VV);
         const int c0 = 32 * tc, d0 = 32 * td;
-        for (int rr = ty; rr < 32; rr += 8) {
+        // all eight loads of a thread in flight before the first store
+        double vcd[4], vdc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int rr = ty + 8 * q;
             const int c = c0 + rr, d = d0 + tx;
-            tcd[rr][tx] = (c < a.V && d < a.V) ? f64_to_f32(T[(long)c * a.V + d]) : 0.0f;   // t[c0+rr][d0+tx]
+            vcd[q] = (c < a.V && d < a.V) ? T[(long)c * a.V + d] : 0.0;      // t[c0+rr][d0+tx]
             const int dd = d0 + rr, cc = c0 + tx;
-            tdc[rr][tx] = (dd < a.V && cc < a.V) ? f64_to_f32(T[(long)dd * a.V + cc]) : 0.0f;  // t[d0+rr][c0+tx]
+            vdc[q] = (dd < a.V && cc < a.V) ? T[(long)dd * a.V + cc] : 0.0;  // t[d0+rr][c0+tx]
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            tcd[ty + 8 * q][tx] = f64_to_f32(vcd[q]);
+            tdc[ty + 8 * q][tx] = f64_to_f32(vdc[q]);
         }
         __syncthreads();
         // threads 0..127: row c = c0 + tid / 4, 8 d from d0 + 8 * (tid % 4)
