@@ -32,5 +32,7 @@ What it computes (arXiv 2401.11935, Section II, Eqs. 2-4):
 Parity status: every function is pinned by tests under ``tests/`` except the
 DC modification term set, which is "parity unpinned" (the term list of the DC
 approximation is defined in the paper's cited DC literature, not in the
-paper; only its switch-off limit, symmetry and invariance are pinned).
+paper; pinned here: its switch-off limit, symmetry and invariance, its
+closed-shell statement, the two-electron limit and the particle-hole
+relabeling, which fixes the balance of its hole and particle terms).
 """

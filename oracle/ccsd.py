@@ -105,8 +105,11 @@ def dc_delta(fr, t2):
       + 1/2 P(ij)P(ab) <mn|fe> t_im^ae t_jn^bf
       + 1/4 P(ij) t_im^ab t_jn^ef <mn||ef>
       + 1/4 P(ab) t_ij^ae t_mn^bf <mn||ef>.
-    Parity unpinned (only its switch-off limit, spin-flip symmetry and
-    orbital-rotation invariance are pinned)."""
+    Parity unpinned against the DC literature.  Pinned: its switch-off
+    limit, spin-flip symmetry and orbital-rotation invariance, equality with
+    the closed-shell list, cancellation for two electrons, and covariance
+    under the particle-hole relabeling (which requires the hole and the
+    particle Fock-like terms to be treated alike)."""
     g = fr.g("oovv")
     gx = fr.g_direct("oovv").transpose(0, 1, 3, 2)  # gx[m,n,e,f] = <mn|fe>
     ring = E("imae,mnef,jnbf->ijab", t2, gx, t2)
