@@ -78,6 +78,54 @@ def test_library_refuses_bad_files(tmp_path):
         L.dcsd_fcidump_header(str(tmp_path / "missing"))
 
 
+_HDR = " &FCI NORB={n},NELEC={ne},MS2={ms},{extra} &END\n"
+_BAD = [
+    # (file text, call, keyword arguments, words of the error message)
+    (" &FCI MS2=0, &END\n", "header", {}, "NORB or NELEC"),
+    (_HDR.format(n=2, ne=2, ms=0, extra="") .replace("NELEC=2,", ""), "header", {}, "NORB or NELEC"),
+    (_HDR.format(n=0, ne=2, ms=0, extra=""), "header", {}, "NORB out of range"),
+    (_HDR.format(n=161, ne=2, ms=0, extra=""), "header", {}, "NORB out of range"),
+    (_HDR.format(n=2, ne=2, ms=0, extra="IUHF=1,"), "header", {}, "unrestricted"),
+    (_HDR.format(n=2, ne=2, ms=0, extra="") + " 0.5 1 x 1 1\n", "read", {}, "malformed integral line 1"),
+    (_HDR.format(n=2, ne=2, ms=0, extra="") + " 0.5 1 1 1 1\n\n 0.25 2 2\n", "read", {}, "malformed integral line 3"),
+    (_HDR.format(n=2, ne=2, ms=0, extra="") + " 0.5 -1 1 1 1\n", "read", {}, "out of range on integral line 1"),
+    (_HDR.format(n=4, ne=4, ms=2, extra="") + " 0.5 1 1 1 1\n", "prepare", {}, "MS2 = 0"),
+    (_HDR.format(n=4, ne=3, ms=0, extra="") + " 0.5 1 1 1 1\n", "prepare", {}, "MS2 = 0"),
+    (_HDR.format(n=4, ne=4, ms=0, extra="") + " 0.5 1 1 1 1\n", "prepare", {"n_frozen": 2}, "frozen-core count"),
+    (_HDR.format(n=3, ne=4, ms=0, extra="") + " 0.5 1 1 1 1\n", "prepare", {}, "at least one virtual"),
+    (_HDR.format(n=4, ne=4, ms=0, extra="") + " 0.5 1 1 1 1\n", "prepare", {"chol_tol": 0.0}, "threshold must be positive"),
+    (_HDR.format(n=4, ne=4, ms=0, extra="") + " -1.0 1 1 0 0\n 0.3 1 2 0 0\n", "prepare", {}, "zero to the Cholesky"),
+]
+
+
+@pytest.mark.parametrize("text,call,kw,words", _BAD)
+def test_library_names_each_bad_input(tmp_path, text, call, kw, words):
+    """Each refusal of the host-side reader and preparation comes back as
+    INVALID_ARG with its own message (no file is read partially)."""
+    from paper_2401_11935_gb300 import _lib as L
+    p = tmp_path / "FCIDUMP"
+    p.write_text(text)
+    fn = {"header": L.dcsd_fcidump_header, "read": L.dcsd_fcidump_read, "prepare": L.dcsd_fcidump_prepare}[call]
+    with pytest.raises(L.DcsdError) as ei:
+        fn(str(p), **kw)
+    assert ei.value.status == 1 and words in str(ei.value), str(ei.value)
+
+
+def test_library_accepts_the_same_inputs_when_valid(tmp_path):
+    """The valid counterparts of the refusals above are read: a header split
+    over lines with ORBSYM, blank lines between integrals, D exponents."""
+    from paper_2401_11935_gb300 import _lib as L
+    p = tmp_path / "FCIDUMP"
+    p.write_text(" &FCI NORB=4,NELEC=4,\n  ORBSYM=1,1,1,1,\n  ISYM=1, MS2=0,\n &END\n"
+                 " 0.5D0 1 1 1 1\n\n 0.25 2 2 2 2\n 0.125 3 3 3 3\n 0.0625 4 4 4 4\n"
+                 " -1.0 1 1 0 0\n -0.5 2 2 0 0\n 0.1 3 3 0 0\n 0.2 4 4 0 0\n 0.75 0 0 0 0\n")
+    assert L.dcsd_fcidump_header(str(p)) == (4, 4, 0)
+    h, eri, ec = L.dcsd_fcidump_read(str(p))
+    assert eri[0, 0, 0, 0] == 0.5 and eri[1, 1, 1, 1] == 0.25 and h[0, 0] == -1.0 and ec == 0.75
+    info, fa, fb, B = L.dcsd_fcidump_prepare(str(p), n_frozen=1)
+    assert info.n_c == 0 and info.n_v == 1
+
+
 @pytest.mark.parametrize("tol", [1e-8, 1e-12])
 def test_cholesky_reproduces_integrals(pin, tol):
     from paper_2401_11935_gb300 import _lib as L
